@@ -1,0 +1,29 @@
+"""Build the plain-C FP64 oracle into a shared library (test infrastructure).
+
+The oracle is compiled with -ffp-contract=off so that every product and sum
+is rounded as written in the source.
+"""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "tts_oracle.c")
+LIB = os.path.join(HERE, "libtts_oracle.so")
+
+
+def build(force: bool = False) -> str:
+    hdr = os.path.join(HERE, "tts_oracle.h")
+    if (not force and os.path.exists(LIB)
+            and os.path.getmtime(LIB) >= max(os.path.getmtime(SRC), os.path.getmtime(hdr))):
+        return LIB
+    tmp = LIB + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-Wall", "-o", tmp, SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv))
