@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the stochastic spin advance (one JSON line).
+
+Workload (default): GdFeCo on a simple-cubic 128^3 lattice (2,097,152 spins)
+x 4 realisations, random 25 % Gd, constant nearest-neighbour exchange, a
+16^3 TTM grid with a Gaussian laser spot (sigma 40 A) calibrated to a 2000 K
+peak, FP32 spins with FP64 TTM, sigma-table and reductions, dt = 0.1 fs.
+One benchmark step = `--chunk` time steps of every spin of every realisation.
+
+Metric: spin-steps/s (one spin advanced by one full dt) over all GPUs, with
+the fraction of the HBM roofline of the dominant kernel.  The reference arm
+(`--impl reference`) times the FP64 CPU oracle on a bounded sample of the
+same workload (one realisation, one dt per benchmark step).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_SPIN_STEP = {32: 25.0, 64: 49.0}   # read s + write s + species byte
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _workload(name):
+    from paper_2608_18541_b300 import workloads as W
+    if name == "gdfeco_128x4":
+        sysd, ttm = W.config_gdfeco_large(128, 4)
+        return sysd, ttm, "GdFeCo sc 128^3 x 4 realisations, 16^3 TTM grid, Gaussian spot 40 A, peak 2000 K"
+    if name == "gdfeco_256x1":
+        sysd, ttm = W.config_gdfeco_large(256, 1)
+        return sysd, ttm, "GdFeCo sc 256^3 x 1 realisation, 16^3 TTM grid, Gaussian spot 40 A, peak 2000 K"
+    if name == "gdfeco_32":
+        sysd, ttm = W.config_gdfeco_32()
+        return sysd, ttm, "GdFeCo sc 32^3, one-cell 2TM, 50 fs pulse to 1500 K"
+    raise SystemExit("unknown workload " + name)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6400.0, "fallback"
+
+
+def _traffic(kernel, precision):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None when it does not match the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = t.get("%s_fp%d" % (kernel, precision))
+    if not e:
+        return None
+    import hashlib
+    src = os.path.join(ROOT, "paper_2608_18541_b300", "csrc", e["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return e["bytes_per_launch"] if h == e.get("source_sha") else None
+
+
+def cpu_oracle_rate(sysd, ttm, steps):
+    """Time the FP64 CPU oracle (single thread) on one realisation."""
+    import oracle as O
+    inst0 = dict(sysd)
+    if inst0.get("instances"):
+        inst0["instances"] = inst0["instances"][:1]
+    o = O.Oracle(inst0, ttm, instance=0)
+    o.step(1)  # first step outside the timing (allocations)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return o.n * steps / dt, o.n, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    sysd, ttm, desc = _workload(args.workload)
+    import oracle as O
+    inst0 = dict(sysd)
+    if inst0.get("instances"):
+        inst0["instances"] = inst0["instances"][:1]
+    o = O.Oracle(inst0, ttm, instance=0)
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    dt = time.perf_counter() - t0
+    v = o.n * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "spin-steps/s", "value": v, "unit": "spin-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": desc, "sample": "one realisation, one dt per step"},
+        "cpu_baseline": {"value": v, "unit": "spin-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": "1 of %d realisations (%d spins), %d steps of dt" % (
+                             len(sysd.get("instances") or [0]), o.n, args.steps)},
+        "e2e": {"value": v, "unit": "spin-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--chunk", type=int, default=100, help="time steps per benchmark step")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="gdfeco_128x4")
+    ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--engine", default="auto")
+    ap.add_argument("--cpu-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import numpy as np
+
+    import paper_2608_18541_b300 as P
+    from paper_2608_18541_b300 import build as B
+
+    if not os.path.exists(P.LIB_PATH):
+        B.build()
+    sysd, ttm, desc = _workload(args.workload)
+    n_inst_local = len(sysd.get("instances") or [0])
+    stream = torch.cuda.current_stream()
+    g = P.System(sysd, ttm, precision=args.precision, engine=args.engine, stream=stream.cuda_stream,
+                 instance_base=rank * n_inst_local)
+    spins = g.n_total
+    for _ in range(args.warmup):
+        g.step(args.chunk)
+    g.sync()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    sampler = ClockSampler(local) if local == 0 else None
+    launches0 = g.info().kernel_launches
+    g.profile_enable(True)
+    barrier()
+    if sampler:
+        sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        g.step(args.chunk)
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = ev0.elapsed_time(ev1)
+    kern_ms, kern_steps, kern_spin_steps = g.profile_read()
+    g.profile_enable(False)
+    launches = g.info().kernel_launches - launches0
+    g.sync()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    tot = torch.tensor([float(spins)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    total_spins = float(tot.item())
+    total_dt = args.steps * args.chunk
+    value = total_spins * total_dt / (ms_max / 1e3)
+
+    # end to end through the public API with host buffers: upload the initial
+    # spins, run the same number of time steps, read spins and observables back
+    host_in = np.ascontiguousarray(g.get_all_spins())
+    host_out = np.empty_like(host_in)
+    barrier()
+    t0 = time.perf_counter()
+    g.set_all_spins(host_in)
+    for _ in range(args.steps):
+        g.step(args.chunk)
+    g.get_all_spins(host_out)
+    obs = g.observe_now(0)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_s = float(te.item())
+    e2e = {"value": total_spins * total_dt / e2e_s, "unit": "spin-steps/s",
+           "h2d_bytes_per_step": int(host_in.nbytes // args.steps),
+           "d2h_bytes_per_step": int((host_out.nbytes + obs.nbytes) // args.steps),
+           "note": "one upload and one read-back of all spins per run, divided over the benchmark steps"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = _peaks()
+    bpu = BYTES_PER_SPIN_STEP[args.precision]
+    kernel_name = "step_" + g.engine
+    achieved = bpu * kern_spin_steps / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+                "traffic": _traffic(kernel_name, args.precision), "kernel": kernel_name,
+                "bytes_per_unit": bpu, "units_per_launch": spins,
+                "avg_launch_ms": kern_ms / max(kern_steps, 1)}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, n1, secs = cpu_oracle_rate(sysd, ttm, args.cpu_steps)
+        cpu = {"value": rate, "unit": "spin-steps/s", "cores": 1, "kind": "oracle",
+               "sample": "1 of %d realisations (%d spins), %d steps of dt, %.1f s" % (
+                   n_inst_local, n1, args.cpu_steps, secs)}
+    line = {
+        "metric": "spin-steps/s", "value": value, "unit": "spin-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
+        "config": {"workload": desc, "spins_per_gpu": spins, "dt_per_step": args.chunk,
+                   "engine": g.engine, "l2": "state and tables exceed L2 (126 MB) per step" if spins * 16 > 126e6
+                   else "working set may fit L2", "parallelism": "instances sharded, dp%d" % world},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

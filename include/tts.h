@@ -1,0 +1,254 @@
+/*
+ * tts.h -- C ABI of the B300 (sm_103a) stochastic spin-dynamics library.
+ *
+ * The library advances classical atomic spins under the stochastic
+ * Landau-Lifshitz-Gilbert equation (paper Eq. 1) with a Langevin bath whose
+ * temperature is the local electron temperature of a two-temperature-model
+ * grid (paper Eq. 2, Sec. II.B, "fix langevin/spin/ttm"), deterministic
+ * torques scaled by 1/mu_i and noise scaled by 1/sqrt(mu_i) (Sec. II.C,
+ * "fix moment/scale/spin" with "mu_fdt"), exchange from a constant or
+ * Bethe-Slater radial J(r) (Sec. II.E), uniaxial anisotropy and a Zeeman field.
+ * The sequential Suzuki-Trotter spin sweep of the paper (Sec. II.A) is done as
+ * a graph-coloured symmetric sweep; many independent realisations (the task-
+ * level replicas of Sec. II.F) advance together as instances of one system.
+ *
+ * Conventions
+ *  - Units: SI, except moments in Bohr magnetons and lengths in angstrom.
+ *  - Every function returns an int status: TTS_OK (0) or a negative TTS_ERR_*.
+ *    tts_last_error() returns a message for the calling thread's last failure.
+ *    No exception or abort crosses this interface.
+ *  - The library owns all device memory of a system.  Host arrays passed in are
+ *    read during the call only; host arrays passed out are written during the
+ *    call only.
+ *  - All work of a system is issued on the CUDA stream given at creation
+ *    (a cudaStream_t passed as void*, NULL = legacy default stream).
+ *    tts_step() returns once the work is queued; calls that return data to
+ *    the host synchronise that stream first.
+ *  - Spin arrays at this interface are in canonical atom order: atom id
+ *    ((iz * ny + iy) * nx + ix) * nbasis + b for lattices (basis order sc: 0;
+ *    bcc: corner, body centre; fcc: (0,0,0), (.5,.5,0), (.5,0,.5), (0,.5,.5)),
+ *    and input order for explicit clusters; three doubles (x, y, z) per atom.
+ *  - One system handle must not be used from two host threads at once.
+ */
+#ifndef TTS_H
+#define TTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define TTS_API __attribute__((visibility("default")))
+#else
+#define TTS_API
+#endif
+
+#define TTS_OK 0
+#define TTS_ERR_ARG (-1)            /* invalid argument or descriptor */
+#define TTS_ERR_CUDA (-2)           /* a CUDA runtime call failed */
+#define TTS_ERR_OOM (-3)            /* device or host allocation failed */
+#define TTS_ERR_DEVICE_TIMEOUT (-4) /* a bounded device-side wait ran out */
+#define TTS_ERR_HEALTH (-5)         /* the device health word flagged a fault */
+#define TTS_ERR_STATE (-6)          /* call not valid in the current state */
+#define TTS_ERR_UNSUPPORTED (-7)    /* combination not implemented */
+
+#define TTS_MAX_SPECIES 2
+#define TTS_NOBS 20
+
+#define TTS_LATTICE_SC 0
+#define TTS_LATTICE_BCC 1
+#define TTS_LATTICE_FCC 2
+#define TTS_LATTICE_CLUSTER 3      /* explicit positions, open boundaries */
+
+#define TTS_EXCH_NONE 0
+#define TTS_EXCH_CONST 1           /* J(r) = J1 for r < rc */
+#define TTS_EXCH_BETHE_SLATER 2    /* J(r) = 4 J1 x (1 - J2 x) exp(-x), x = (r/J3)^2, r < rc (Sec. II.E) */
+
+#define TTS_ENGINE_AUTO 0          /* pick the fastest engine valid for the system */
+#define TTS_ENGINE_GENERAL 1       /* explicit neighbour table, one launch per colour pass */
+#define TTS_ENGINE_CHECKER 2       /* sc lattice, even edges: implicit stencil, fused passes */
+#define TTS_ENGINE_RESIDENT 3      /* sc lattice: one instance per CTA held in shared memory */
+
+/* Exchange coupling of one species pair.  The pair energy is -J(r) s_i.s_j. */
+typedef struct {
+    int kind;       /* TTS_EXCH_* */
+    double J1;      /* J */
+    double J2;      /* dimensionless (Bethe-Slater) */
+    double J3;      /* angstrom (Bethe-Slater) */
+    double rc;      /* cutoff, angstrom */
+} tts_exchange;
+
+/* System description.  Hamiltonian (paper Sec. II.A, II.C):
+ *   E = -sum_{i<j} J_ij s_i.s_j - sum_i K_{t_i} (s_i.n)^2 - sum_i mu_i B.s_i
+ * and the field of atom i is B_i = -(1/mu_i) dE/ds_i in tesla. */
+typedef struct {
+    int lattice;                 /* TTS_LATTICE_* */
+    int nx, ny, nz;              /* conventional cells of every instance (overridable) */
+    double a;                    /* lattice constant, angstrom */
+    int n_explicit;              /* cluster: atom count */
+    const double *pos_explicit;  /* cluster: 3 * n_explicit positions, angstrom */
+    const int *species_explicit; /* cluster: species per atom (NULL = all 0) */
+    int nspecies;                /* 1 or 2 */
+    double mu_muB[TTS_MAX_SPECIES];   /* moments, Bohr magnetons */
+    double frac1;                /* fraction of lattice sites holding species 1 */
+    tts_exchange exch[TTS_MAX_SPECIES][TTS_MAX_SPECIES]; /* must be symmetric */
+    double K[TTS_MAX_SPECIES];   /* uniaxial anisotropy energy per atom, J */
+    double axis[3];              /* anisotropy axis (normalised by the library) */
+    double B[3];                 /* applied field, T */
+    double alpha[TTS_MAX_SPECIES];    /* Gilbert damping */
+    double dt;                   /* time step, s */
+    double T_bath;               /* bath temperature while no TTM grid is set, K */
+    double init_dir[TTS_MAX_SPECIES][3]; /* initial spin direction per species */
+    uint64_t seed;               /* noise and placement key */
+    int precision;               /* 32 (float spins) or 64 (double spins) */
+    int sample_every;            /* observables every this many steps; 0 = never */
+    int obs_capacity;            /* samples kept per instance (ring); 0 = 1024 */
+    int n_instances;             /* independent realisations, >= 1 */
+    const int *inst_cells;       /* NULL or 3 * n_instances cell counts (lattices) */
+    const double *inst_frac1;    /* NULL or n_instances species-1 fractions */
+    const double *inst_peak_Te;  /* NULL or n_instances TTM peak temperatures, K */
+    const double *inst_fwhm;     /* NULL or n_instances TTM pulse FWHM, s */
+    int engine;                  /* TTS_ENGINE_* */
+    int instance_base;           /* global id of instance 0 (Philox counter word 3 and
+                                    placement stream are keyed by instance_base + index) */
+} tts_system_desc;
+
+#define TTS_SOURCE_NONE 0
+#define TTS_SOURCE_PEAK 1          /* calibrate P0 so that max T_e over cells and steps = peak_Te */
+#define TTS_SOURCE_POWER 2         /* use P0 as given */
+
+#define TTS_SPATIAL_UNIFORM 0
+#define TTS_SPATIAL_XY_GAUSS 1     /* exp(-((x-xc)^2 + (y-yc)^2) / (2 sigma_xy^2)) at cell centres */
+#define TTS_SPATIAL_Z_EXP 2        /* exp(-z / depth_z) at cell centres */
+
+/* Two-temperature-model grid ("fix ttm" of Sec. II.B), one per instance,
+ * periodic, covering the instance's box: explicit update of the electron
+ * energy gamma_e T_e^2 / 2 with diffusion kappa_e, exchange G (T_e - T_l) and
+ * a source P0 exp(-(t - t0)^2 / (2 sigma_t^2)) f(r), sigma_t = fwhm / (2 sqrt(2 ln 2)). */
+typedef struct {
+    int cells[3];
+    double gamma_e;   /* J m^-3 K^-2 */
+    double C_l;       /* J m^-3 K^-1 */
+    double G;         /* W m^-3 K^-1 */
+    double kappa_e;   /* W m^-1 K^-1 */
+    double T0;        /* initial T_e = T_l, K */
+    int source;       /* TTS_SOURCE_* */
+    double peak_Te;   /* K (per-instance override in the system description) */
+    double P0;        /* W m^-3 */
+    double fwhm;      /* s (per-instance override in the system description) */
+    double t0;        /* pulse centre, s; negative = 3 sigma_t */
+    int spatial;      /* TTS_SPATIAL_* */
+    double sigma_xy;  /* angstrom */
+    double depth_z;   /* angstrom */
+} tts_ttm_desc;
+
+typedef struct tts_system tts_system;
+
+/* Facts about a created system. */
+typedef struct {
+    int64_t n_total;        /* atoms over all instances */
+    int n_instances;
+    int engine;             /* TTS_ENGINE_* in use */
+    int precision;          /* 32 or 64 */
+    int max_colours;        /* largest colour count over instances */
+    int64_t steps_done;     /* steps completed (device step counter as last synchronised) */
+    int64_t kernel_launches;/* kernels this library has launched for the system so far */
+} tts_info_t;
+
+/* Build a system: lattice sites, random alloy placement (exactly
+ * round(frac1 * N) sites of species 1 per instance, sampled without
+ * replacement as in Sec. II.D, drawn from Philox4x32-10 with key = seed and
+ * counter (k, attempt, 0xFFFF0000, instance)), neighbour lists, colour
+ * classes, device buffers.  Spins start along init_dir of their species and
+ * the bath is T_bath until tts_set_ttm_grid().  stream: cudaStream_t or NULL.
+ * Errors: TTS_ERR_ARG (bad descriptor, box edge not above twice the cutoff),
+ * TTS_ERR_OOM, TTS_ERR_CUDA, TTS_ERR_UNSUPPORTED (engine forced on a system it
+ * cannot run).  On error *out is set to NULL. */
+TTS_API int tts_create_system(const tts_system_desc *desc, void *stream, tts_system **out);
+
+/* Free all memory of a system (synchronises its stream).  NULL is allowed. */
+TTS_API int tts_destroy(tts_system *sys);
+
+/* Attach a TTM grid to every instance (Eq. 2: each atom's bath temperature
+ * is T_e of the grid cell that holds it).  Calibrates P0 per instance when
+ * source == TTS_SOURCE_PEAK.  Resets T_e = T_l = T0.  Errors: TTS_ERR_ARG,
+ * TTS_ERR_UNSUPPORTED (clusters), TTS_ERR_CUDA. */
+TTS_API int tts_set_ttm_grid(tts_system *sys, const tts_ttm_desc *ttm);
+
+/* Advance every instance by nsteps time steps (asynchronous).  One step:
+ * noise amplitudes from T_e(t_n); the symmetric colour sweep; the TTM grid
+ * from t_n to t_n+1; observables at t_n+1 when the step count reaches a
+ * multiple of sample_every.  Errors: TTS_ERR_ARG (nsteps < 0), TTS_ERR_CUDA. */
+TTS_API int tts_step(tts_system *sys, int64_t nsteps);
+
+/* Wait for queued work and check the device health word.  Errors:
+ * TTS_ERR_HEALTH (non-finite spin), TTS_ERR_DEVICE_TIMEOUT, TTS_ERR_CUDA. */
+TTS_API int tts_sync(tts_system *sys);
+
+/* Copy up to max_samples observable records of one instance, oldest first,
+ * TTS_NOBS doubles each:
+ *  [0] t  [1..3] mean s of species 0  [4..6] mean s of species 1
+ *  [7..9] sum(mu_i s_i)/sum(mu_i)  [10] -sum_{i<j} J_ij s_i.s_j
+ *  [11] -sum K (s.n)^2  [12] -sum mu_i B.s_i  [13..14] spin temperature per
+ *  species, sum|s x H|^2 / (2 k_B sum s.H) with H = mu_i B_i
+ *  [15] mean T_e  [16] mean T_l  [17..18] reserved (0)  [19] step count.
+ * *n_written receives the count.  Synchronises. */
+TTS_API int tts_observables(tts_system *sys, int inst, double *out_host, int64_t max_samples,
+                    int64_t *n_written);
+
+/* Record one observable row for an instance now, into out_host (TTS_NOBS
+ * doubles), without touching the ring.  Synchronises. */
+TTS_API int tts_observe_now(tts_system *sys, int inst, double *out_host);
+
+/* Spins of one instance, 3 doubles per atom, canonical order.  Synchronises. */
+TTS_API int tts_get_spins(tts_system *sys, int inst, double *host_xyz);
+/* Replace the spins of one instance (normalised by the library). */
+TTS_API int tts_set_spins(tts_system *sys, int inst, const double *host_xyz);
+/* Spins of all instances, concatenated in instance order (3 doubles each). */
+TTS_API int tts_get_all_spins(tts_system *sys, double *host_xyz);
+TTS_API int tts_set_all_spins(tts_system *sys, const double *host_xyz);
+
+/* Atom count, species (int per atom) and colour class (int per atom) of one
+ * instance, canonical order. */
+TTS_API int tts_instance_size(tts_system *sys, int inst, int64_t *n_atoms, int *n_colours);
+TTS_API int tts_get_species(tts_system *sys, int inst, int *host_species);
+TTS_API int tts_get_colours(tts_system *sys, int inst, int *host_colours);
+
+/* T_e, T_l of an instance's grid cells (x fastest) and its source power P0. */
+TTS_API int tts_get_ttm(tts_system *sys, int inst, double *host_Te, double *host_Tl, double *P0);
+TTS_API int tts_set_ttm_state(tts_system *sys, int inst, const double *host_Te, const double *host_Tl);
+
+/* The step counter (the Philox step word and the time t = step * dt). */
+TTS_API int tts_get_step(tts_system *sys, int64_t *step);
+TTS_API int tts_set_step(tts_system *sys, int64_t step);
+
+/* Checkpoint: every piece of dynamic state (spins, TTM grids, step counter,
+ * observable rings) in an opaque byte string.  With buf == NULL, *nbytes
+ * receives the size needed.  Restoring into a system created from the same
+ * description and continuing reproduces an uninterrupted run bit for bit. */
+TTS_API int tts_get_state(tts_system *sys, void *buf, size_t *nbytes);
+TTS_API int tts_set_state(tts_system *sys, const void *buf, size_t nbytes);
+
+TTS_API int tts_info(tts_system *sys, tts_info_t *info);
+
+/* Kernel timing.  While enabled, tts_step launches each step's kernels one by
+ * one instead of replaying the captured graph, and brackets the step's
+ * dominant kernels (the colour passes, or the fused step kernel of a fast
+ * engine) with CUDA events on the system's stream.  No work is skipped. */
+TTS_API int tts_profile_enable(tts_system *sys, int enable);
+/* Total duration in ms of the bracketed kernels since profiling was enabled,
+ * the number of steps bracketed, and the spin-steps those steps completed
+ * (atoms x steps).  Synchronises the stream. */
+TTS_API int tts_profile_read(tts_system *sys, double *ms, int64_t *steps, int64_t *spin_steps);
+
+/* Message of the calling thread's last failed call (never NULL). */
+TTS_API const char *tts_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTS_H */

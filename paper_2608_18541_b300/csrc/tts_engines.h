@@ -1,0 +1,45 @@
+// tts_engines.h -- hooks of the fast engines (checkerboard and resident).
+//
+// The general engine keeps the canonical device state (slot-ordered spin
+// arrays, TTM grids, observables).  A fast engine may keep spins in its own
+// layout; it then provides the step recording and the spin transfers below,
+// and copies its spins into the general arrays when observables or
+// checkpoints need them.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "tts_internal.h"
+#include "tts_kernels.h"
+
+namespace tts {
+
+struct EngineState;
+
+// Returns the engine that will run the system (TTS_ENGINE_*), or -1 when the
+// requested engine (or, for AUTO, every fast engine) cannot run it.
+int engine_select(const tts_system_desc &d, const std::vector<HostInstance> &host, int requested);
+
+int engine_create(const tts_system_desc &d, const std::vector<HostInstance> &host,
+                  const std::vector<std::vector<int64_t>> &slot_of_atom, const std::vector<DevInstance> &dinst,
+                  const StepParams &p, const DevBuffers &b, int engine, cudaStream_t st, EngineState **out);
+void engine_destroy(EngineState *e);
+const char *engine_last_error();
+
+// Issue the kernels of one step on stream st (captured into a graph, or run
+// directly while profiling).  ev_begin / ev_end, when not null, are recorded
+// around the step's dominant kernels.
+cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuffers &b, const TtmParams &tp,
+                               bool ttm_active, cudaStream_t st, int *kernels, cudaEvent_t ev_begin,
+                               cudaEvent_t ev_end);
+// Spins of one instance in general slot order (relative to the instance).
+int engine_read_spins(EngineState *e, int inst, void *x, void *y, void *z, cudaStream_t st);
+int engine_write_spins(EngineState *e, int inst, const void *x, const void *y, const void *z, cudaStream_t st);
+// A TTM grid was attached: new cell map in general slot order.
+int engine_set_cells(EngineState *e, const std::vector<DevInstance> &dinst, const std::vector<int> &cellmap,
+                     cudaStream_t st);
+cudaError_t engine_sync_to_general(EngineState *e, const DevBuffers &b, cudaStream_t st);
+cudaError_t engine_sync_from_general(EngineState *e, const DevBuffers &b, cudaStream_t st);
+
+}  // namespace tts

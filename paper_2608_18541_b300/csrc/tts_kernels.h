@@ -1,0 +1,67 @@
+// tts_kernels.h -- launchers of the device kernels (implemented in tts_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "tts_internal.h"
+
+namespace tts {
+
+// Parameters passed by value to every step kernel.
+struct StepParams {
+    SpeciesParams sp[TTS_MAX_SPECIES];
+    double axis[3];
+    double B[3];
+    double dt;
+    uint32_t key0, key1;
+    int nspecies;
+    int64_t n_total;         // slots
+    int zmax;                // neighbour-table width (general engine)
+    int n_instances;
+    int instance_base;       // global id of instance 0 (Philox counter word 3)
+    int sample_every;
+    int obs_capacity;
+};
+
+// Device buffers of a system (general engine layout, real_t = float or double).
+struct DevBuffers {
+    void *sx = nullptr, *sy = nullptr, *sz = nullptr;   // spins, slot order
+    int *atom = nullptr;          // canonical atom id of each slot
+    uint8_t *species = nullptr;   // species of each slot
+    int *cell = nullptr;          // global TTM cell of each slot
+    int *nbr = nullptr;           // zmax * n_total neighbour slots (column-major)
+    void *nbr_w = nullptr;        // zmax * n_total J_ij / mu_i (tesla), real_t
+    void *sigma = nullptr;        // ncells * 2 species * 2 (h = dt/2, dt), real_t
+    double *Te = nullptr, *Tl = nullptr;   // per global cell
+    double *src_shape = nullptr;  // per global cell
+    double *ttm_scratch = nullptr;// 2 * ncells
+    double *src_energy = nullptr; // per instance, J
+    DevInstance *inst = nullptr;  // per instance
+    PassRange *ranges = nullptr;  // concatenated over passes
+    int64_t *step = nullptr;      // device step counter
+    unsigned int *health = nullptr;
+    double *obs_partial = nullptr;// per observable block, kObsFields doubles
+    int *obs_block_inst = nullptr;// instance of each observable block
+    int64_t *obs_block_begin = nullptr; // first slot of each observable block
+    double *obs_ring = nullptr;   // n_instances * capacity * TTS_NOBS
+    int64_t *obs_count = nullptr; // samples taken per instance
+    double *obs_now = nullptr;    // n_instances * TTS_NOBS
+};
+
+constexpr int kObsFields = 24;       // per species: 12 partial sums
+constexpr int kObsBlock = 128;       // threads of an observable block
+
+enum HealthBits : unsigned int {
+    kHealthNonFinite = 1u,
+    kHealthTimeout = 2u,
+};
+
+cudaError_t launch_sigma(const StepParams &p, const DevBuffers &b, int ncells_total, int precision,
+                         cudaStream_t st);
+cudaError_t launch_pass_general(const StepParams &p, const DevBuffers &b, int precision, int pass,
+                                int64_t range_offset, int nranges, int64_t nwork, cudaStream_t st);
+cudaError_t launch_ttm(const StepParams &p, const DevBuffers &b, const TtmParams &tp, int n_instances,
+                       cudaStream_t st);
+cudaError_t launch_obs(const StepParams &p, const DevBuffers &b, int precision, int nblocks, int mode,
+                       cudaStream_t st);
+
+}  // namespace tts

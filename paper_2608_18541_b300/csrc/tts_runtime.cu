@@ -1,0 +1,1071 @@
+// tts_runtime.cu -- the C ABI of include/tts.h: system construction, device
+// memory, the captured per-step CUDA graph, TTM set-up and calibration,
+// observables, checkpoints.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tts_engines.h"
+#include "tts_internal.h"
+#include "tts_kernels.h"
+
+using namespace tts;
+
+namespace {
+
+thread_local std::string g_error = "no error";
+
+int fail(int code, const std::string &msg)
+{
+    g_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    g_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? TTS_ERR_OOM : TTS_ERR_CUDA;
+}
+
+#define TTS_CUDA(call, what)                          \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+}  // namespace
+
+struct tts_system {
+    tts_system_desc desc{};
+    int precision = 32;
+    size_t rsize = 4;
+    int engine = TTS_ENGINE_GENERAL;
+    cudaStream_t stream = nullptr;     // caller's stream
+    cudaStream_t capture = nullptr;    // private stream used only to capture graphs
+    int64_t n_total = 0;
+    int n_inst = 0;
+    int zmax = 0;
+    int max_colours = 1;
+    int max_passes = 1;
+    std::vector<HostInstance> host;                 // built instances (canonical order)
+    std::vector<std::vector<int64_t>> slot_of_atom; // per instance: atom -> slot (relative)
+    std::vector<DevInstance> dinst;
+    std::vector<PassRange> ranges;
+    std::vector<int64_t> pass_offset;               // ranges of pass p: [off[p], off[p+1])
+    std::vector<int64_t> pass_work;
+    int ncells_total = 0;
+    bool ttm_active = false;
+    TtmParams tp{};
+    std::vector<double> P0;                         // per instance
+    std::vector<double> inst_peak, inst_fwhm;       // per-instance pulse overrides (may be empty)
+    int obs_blocks = 0;
+    int obs_capacity = 1024;
+    DevBuffers b;
+    StepParams p{};
+    cudaGraphExec_t graph = nullptr;
+    int kernels_per_step = 0;
+    int64_t launches = 0;
+    bool dirty = true;
+    EngineState *eng = nullptr;                     // fast-engine state, if any
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_events;           // begin/end pairs of profiled steps
+    double prof_ms = 0.0;
+    int64_t prof_steps = 0;
+};
+
+namespace {
+
+void free_buffers(tts_system *s)
+{
+    DevBuffers &b = s->b;
+    void *ptrs[] = {b.sx, b.sy, b.sz, b.atom, b.species, b.cell, b.nbr, b.nbr_w, b.sigma, b.Te, b.Tl,
+                    b.src_shape, b.ttm_scratch, b.src_energy, b.inst, b.ranges, b.step, b.health,
+                    b.obs_partial, b.obs_block_inst, b.obs_block_begin, b.obs_ring, b.obs_count, b.obs_now};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    s->b = DevBuffers{};
+}
+
+template <typename T>
+int dev_alloc(T **ptr, size_t count, const char *what)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_error = std::string("cudaMalloc of ") + what + " failed: " + cudaGetErrorString(e);
+        return TTS_ERR_OOM;
+    }
+    *ptr = static_cast<T *>(q);
+    return TTS_OK;
+}
+
+int upload(void *dst, const void *src, size_t bytes, cudaStream_t st, const char *what)
+{
+    if (bytes == 0) return TTS_OK;
+    TTS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), what);
+    TTS_CUDA(cudaStreamSynchronize(st), what);
+    return TTS_OK;
+}
+
+int validate(const tts_system_desc &d)
+{
+    if (d.nspecies < 1 || d.nspecies > TTS_MAX_SPECIES) return fail(TTS_ERR_ARG, "nspecies must be 1 or 2");
+    if (d.precision != 32 && d.precision != 64) return fail(TTS_ERR_ARG, "precision must be 32 or 64");
+    if (!(d.dt > 0.0)) return fail(TTS_ERR_ARG, "dt must be positive");
+    if (d.n_instances < 1) return fail(TTS_ERR_ARG, "n_instances must be >= 1");
+    if (d.lattice < 0 || d.lattice > 3) return fail(TTS_ERR_ARG, "unknown lattice");
+    if (d.lattice != TTS_LATTICE_CLUSTER && !(d.a > 0.0)) return fail(TTS_ERR_ARG, "lattice constant must be positive");
+    if (d.lattice == TTS_LATTICE_CLUSTER && d.n_instances != 1)
+        return fail(TTS_ERR_ARG, "explicit clusters take one instance");
+    for (int t = 0; t < d.nspecies; ++t) {
+        if (!(d.mu_muB[t] > 0.0)) return fail(TTS_ERR_ARG, "moments must be positive");
+        if (!(d.alpha[t] >= 0.0)) return fail(TTS_ERR_ARG, "damping must be >= 0");
+        const double *v = d.init_dir[t];
+        if (!(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] > 0.0)) return fail(TTS_ERR_ARG, "zero initial direction");
+    }
+    for (int a = 0; a < d.nspecies; ++a)
+        for (int c = 0; c < d.nspecies; ++c) {
+            const tts_exchange &x = d.exch[a][c], &y = d.exch[c][a];
+            if (x.kind < 0 || x.kind > 2) return fail(TTS_ERR_ARG, "unknown exchange kind");
+            if (x.kind != y.kind || x.J1 != y.J1 || x.J2 != y.J2 || x.J3 != y.J3 || x.rc != y.rc)
+                return fail(TTS_ERR_ARG, "exchange table must be symmetric");
+            if (x.kind == TTS_EXCH_BETHE_SLATER && !(x.J3 > 0.0)) return fail(TTS_ERR_ARG, "J3 must be positive");
+        }
+    if (!(d.T_bath >= 0.0)) return fail(TTS_ERR_ARG, "T_bath must be >= 0");
+    if (d.engine < 0 || d.engine > 3) return fail(TTS_ERR_ARG, "unknown engine");
+    if (d.sample_every < 0) return fail(TTS_ERR_ARG, "sample_every must be >= 0");
+    if (d.instance_base < 0) return fail(TTS_ERR_ARG, "instance_base must be >= 0");
+    return TTS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// TTM set-up on the host: cell of each atom, source shape, sub-steps and the
+// calibration of P0 (bisection on a TTM-only run).
+// ---------------------------------------------------------------------------
+struct HostTtm {
+    int cells[3];
+    double dx[3], vol;
+    int substeps;
+    double sigma_t, t0;
+    std::vector<double> shape;
+};
+
+int make_host_ttm(const tts_system_desc &d, const HostInstance &hi, const tts_ttm_desc &t, double fwhm, HostTtm *o)
+{
+    int resolved = 0;
+    double dxmin = 0.0;
+    o->vol = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        o->cells[k] = t.cells[k];
+        o->dx[k] = hi.box[k] * kAngstrom / t.cells[k];
+        o->vol *= o->dx[k];
+        if (t.cells[k] > 1) {
+            dxmin = resolved ? std::min(dxmin, o->dx[k]) : o->dx[k];
+            ++resolved;
+        }
+    }
+    o->substeps = 1;
+    if (resolved > 0 && t.kappa_e > 0.0) {
+        const double limit = 0.4 * t.gamma_e * t.T0 * dxmin * dxmin / (t.kappa_e * resolved);
+        const double m = std::ceil(d.dt / limit);
+        o->substeps = m < 1.0 ? 1 : static_cast<int>(m);
+    }
+    o->sigma_t = fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+    o->t0 = t.t0 >= 0.0 ? t.t0 : 3.0 * o->sigma_t;
+    const int nc = t.cells[0] * t.cells[1] * t.cells[2];
+    o->shape.assign(nc, 1.0);
+    for (int cz = 0; cz < t.cells[2]; ++cz)
+        for (int cy = 0; cy < t.cells[1]; ++cy)
+            for (int cx = 0; cx < t.cells[0]; ++cx) {
+                const int c = (cz * t.cells[1] + cy) * t.cells[0] + cx;
+                const double x = (cx + 0.5) * hi.box[0] / t.cells[0];
+                const double y = (cy + 0.5) * hi.box[1] / t.cells[1];
+                const double z = (cz + 0.5) * hi.box[2] / t.cells[2];
+                if (t.spatial == TTS_SPATIAL_XY_GAUSS) {
+                    const double rx = x - 0.5 * hi.box[0], ry = y - 0.5 * hi.box[1];
+                    o->shape[c] = std::exp(-(rx * rx + ry * ry) / (2.0 * t.sigma_xy * t.sigma_xy));
+                } else if (t.spatial == TTS_SPATIAL_Z_EXP) {
+                    o->shape[c] = std::exp(-z / t.depth_z);
+                }
+            }
+    return TTS_OK;
+}
+
+// Largest T_e over cells and step times of a TTM-only run with source power P0.
+double ttm_peak(const tts_system_desc &d, const tts_ttm_desc &t, const HostTtm &h, double P0)
+{
+    const int nx = h.cells[0], ny = h.cells[1], nz = h.cells[2], nc = nx * ny * nz;
+    std::vector<double> Te(nc, t.T0), Tl(nc, t.T0), dE(nc);
+    const int64_t nsteps = static_cast<int64_t>(std::ceil((h.t0 + 10.0 * h.sigma_t) / d.dt));
+    const double delta = d.dt / h.substeps;
+    double peak = t.T0;
+    for (int64_t n = 0; n < nsteps; ++n) {
+        for (int k = 0; k < h.substeps; ++k) {
+            const double tt = double(n) * d.dt + double(k) * delta;
+            const double z = (tt - h.t0) / h.sigma_t;
+            const double pulse = P0 * std::exp(-0.5 * z * z);
+            for (int cz = 0; cz < nz; ++cz)
+                for (int cy = 0; cy < ny; ++cy)
+                    for (int cx = 0; cx < nx; ++cx) {
+                        const int c = (cz * ny + cy) * nx + cx;
+                        double lap = 0.0;
+                        if (nx > 1)
+                            lap += (Te[(cz * ny + cy) * nx + (cx + 1) % nx] - 2.0 * Te[c] +
+                                    Te[(cz * ny + cy) * nx + (cx + nx - 1) % nx]) / (h.dx[0] * h.dx[0]);
+                        if (ny > 1)
+                            lap += (Te[(cz * ny + (cy + 1) % ny) * nx + cx] - 2.0 * Te[c] +
+                                    Te[(cz * ny + (cy + ny - 1) % ny) * nx + cx]) / (h.dx[1] * h.dx[1]);
+                        if (nz > 1)
+                            lap += (Te[(((cz + 1) % nz) * ny + cy) * nx + cx] - 2.0 * Te[c] +
+                                    Te[(((cz + nz - 1) % nz) * ny + cy) * nx + cx]) / (h.dx[2] * h.dx[2]);
+                        const double x = t.G * (Te[c] - Tl[c]);
+                        dE[c] = delta * (t.kappa_e * lap - x + pulse * h.shape[c]);
+                        Tl[c] += delta * x / t.C_l;
+                    }
+            for (int c = 0; c < nc; ++c) Te[c] = std::sqrt(2.0 * (0.5 * t.gamma_e * Te[c] * Te[c] + dE[c]) / t.gamma_e);
+        }
+        for (int c = 0; c < nc; ++c) peak = std::max(peak, Te[c]);
+    }
+    return peak;
+}
+
+double calibrate_P0(const tts_system_desc &d, const tts_ttm_desc &t, const HostTtm &h, double target)
+{
+    const double need = 0.5 * t.gamma_e * (target * target - t.T0 * t.T0);
+    double hi = need / (h.sigma_t * std::sqrt(2.0 * M_PI));
+    while (ttm_peak(d, t, h, hi) < target) hi *= 2.0;
+    double lo = 0.0;
+    for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (ttm_peak(d, t, h, mid) < target) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// ---------------------------------------------------------------------------
+// General-engine layout and upload
+// ---------------------------------------------------------------------------
+template <typename R>
+int upload_general(tts_system *s)
+{
+    const int64_t N = s->n_total;
+    std::vector<int> atom(N), cell(N), nbr(size_t(s->zmax) * N);
+    std::vector<uint8_t> spc(N);
+    std::vector<R> w(size_t(s->zmax) * N), sx(N), sy(N), sz(N);
+    for (int i = 0; i < s->n_inst; ++i) {
+        const HostInstance &hi = s->host[i];
+        const DevInstance &di = s->dinst[i];
+        for (int64_t a = 0; a < hi.n; ++a) {
+            const int64_t slot = di.slot_begin + s->slot_of_atom[i][a];
+            atom[slot] = static_cast<int>(a);
+            spc[slot] = hi.species[a];
+            cell[slot] = di.cell_begin;  // uniform bath: one cell per instance until a TTM grid is set
+            const double inv_mu = 1.0 / (s->desc.mu_muB[hi.species[a]] * kBohrMagneton);
+            const int64_t b0 = hi.nbr_begin[a], b1 = hi.nbr_begin[a + 1];
+            for (int k = 0; k < s->zmax; ++k) {
+                const size_t e = size_t(k) * N + slot;
+                if (b0 + k < b1) {
+                    nbr[e] = static_cast<int>(di.slot_begin + s->slot_of_atom[i][hi.nbr[b0 + k]]);
+                    w[e] = static_cast<R>(hi.nbr_J[b0 + k] * inv_mu);
+                } else {
+                    nbr[e] = static_cast<int>(slot);
+                    w[e] = R(0);
+                }
+            }
+            const double *v = s->desc.init_dir[hi.species[a]];
+            const double m = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            sx[slot] = static_cast<R>(v[0] / m);
+            sy[slot] = static_cast<R>(v[1] / m);
+            sz[slot] = static_cast<R>(v[2] / m);
+        }
+    }
+    DevBuffers &b = s->b;
+    int rc;
+    if ((rc = upload(b.atom, atom.data(), N * sizeof(int), s->stream, "upload atom ids"))) return rc;
+    if ((rc = upload(b.species, spc.data(), N, s->stream, "upload species"))) return rc;
+    if ((rc = upload(b.cell, cell.data(), N * sizeof(int), s->stream, "upload cells"))) return rc;
+    if ((rc = upload(b.nbr, nbr.data(), nbr.size() * sizeof(int), s->stream, "upload neighbours"))) return rc;
+    if ((rc = upload(b.nbr_w, w.data(), w.size() * sizeof(R), s->stream, "upload couplings"))) return rc;
+    if ((rc = upload(b.sx, sx.data(), N * sizeof(R), s->stream, "upload spins"))) return rc;
+    if ((rc = upload(b.sy, sy.data(), N * sizeof(R), s->stream, "upload spins"))) return rc;
+    if ((rc = upload(b.sz, sz.data(), N * sizeof(R), s->stream, "upload spins"))) return rc;
+    return TTS_OK;
+}
+
+int alloc_cells(tts_system *s, int ncells_total)
+{
+    DevBuffers &b = s->b;
+    for (void *q : {(void *)b.Te, (void *)b.Tl, (void *)b.src_shape, (void *)b.ttm_scratch, b.sigma})
+        if (q) cudaFree(q);
+    b.Te = b.Tl = b.src_shape = b.ttm_scratch = nullptr;
+    b.sigma = nullptr;
+    int rc;
+    if ((rc = dev_alloc(&b.Te, ncells_total, "T_e"))) return rc;
+    if ((rc = dev_alloc(&b.Tl, ncells_total, "T_l"))) return rc;
+    if ((rc = dev_alloc(&b.src_shape, ncells_total, "source shape"))) return rc;
+    if ((rc = dev_alloc(&b.ttm_scratch, 2 * size_t(ncells_total), "TTM scratch"))) return rc;
+    char *sig = nullptr;
+    if ((rc = dev_alloc(&sig, size_t(ncells_total) * TTS_MAX_SPECIES * 2 * s->rsize, "sigma table"))) return rc;
+    b.sigma = sig;
+    s->ncells_total = ncells_total;
+    return TTS_OK;
+}
+
+// Issue the kernels of one step on stream c.  ev0 / ev1 (may be null) are
+// recorded around the dominant kernels (the colour passes).
+cudaError_t record_step(tts_system *s, cudaStream_t c, int *kernels, cudaEvent_t ev0, cudaEvent_t ev1)
+{
+    *kernels = 0;
+    if (s->eng) return engine_record_step(s->eng, s->p, s->b, s->tp, s->ttm_active, c, kernels, ev0, ev1);
+    cudaError_t e = launch_sigma(s->p, s->b, s->ncells_total, s->precision, c);
+    ++*kernels;
+    if (e == cudaSuccess && ev0) e = cudaEventRecord(ev0, c);
+    for (int pass = 0; pass < s->max_passes && e == cudaSuccess; ++pass) {
+        const int64_t off = s->pass_offset[pass];
+        const int nr = static_cast<int>(s->pass_offset[pass + 1] - off);
+        e = launch_pass_general(s->p, s->b, s->precision, pass, off, nr, s->pass_work[pass], c);
+        ++*kernels;
+    }
+    if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, c);
+    if (e == cudaSuccess && s->ttm_active) {
+        e = launch_ttm(s->p, s->b, s->tp, s->n_inst, c);
+        ++*kernels;
+    }
+    if (e == cudaSuccess) {
+        e = launch_obs(s->p, s->b, s->precision, s->obs_blocks, 0, c);
+        *kernels += 2;
+    }
+    return e;
+}
+
+int build_graph(tts_system *s)
+{
+    if (s->graph) {
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+    }
+    cudaStream_t c = s->capture;
+    TTS_CUDA(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int kernels = 0;
+    cudaError_t e = record_step(s, c, &kernels, nullptr, nullptr);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(e, "record step");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
+    e = cudaGraphInstantiate(&s->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "instantiate step graph");
+    s->kernels_per_step = kernels;
+    s->dirty = false;
+    return TTS_OK;
+}
+
+void drop_profile_events(tts_system *s)
+{
+    for (cudaEvent_t ev : s->prof_events) cudaEventDestroy(ev);
+    s->prof_events.clear();
+}
+
+int check_inst(tts_system *s, int inst)
+{
+    if (!s) return fail(TTS_ERR_ARG, "null system");
+    if (inst < 0 || inst >= s->n_inst) return fail(TTS_ERR_ARG, "instance index out of range");
+    return TTS_OK;
+}
+
+template <typename R>
+int read_instance_spins(tts_system *s, int inst, double *out)
+{
+    const DevInstance &di = s->dinst[inst];
+    std::vector<R> x(di.n), y(di.n), z(di.n);
+    if (s->eng) {
+        int rc = engine_read_spins(s->eng, inst, x.data(), y.data(), z.data(), s->stream);
+        if (rc) return fail(rc, "engine spin read failed");
+    } else {
+        const size_t off = di.slot_begin * sizeof(R);
+        TTS_CUDA(cudaMemcpyAsync(x.data(), static_cast<char *>(s->b.sx) + off, di.n * sizeof(R), cudaMemcpyDeviceToHost, s->stream), "read spins");
+        TTS_CUDA(cudaMemcpyAsync(y.data(), static_cast<char *>(s->b.sy) + off, di.n * sizeof(R), cudaMemcpyDeviceToHost, s->stream), "read spins");
+        TTS_CUDA(cudaMemcpyAsync(z.data(), static_cast<char *>(s->b.sz) + off, di.n * sizeof(R), cudaMemcpyDeviceToHost, s->stream), "read spins");
+        TTS_CUDA(cudaStreamSynchronize(s->stream), "read spins");
+    }
+    const std::vector<int64_t> &so = s->slot_of_atom[inst];
+    for (int64_t a = 0; a < di.n; ++a) {
+        out[3 * a] = x[so[a]];
+        out[3 * a + 1] = y[so[a]];
+        out[3 * a + 2] = z[so[a]];
+    }
+    return TTS_OK;
+}
+
+template <typename R>
+int write_instance_spins(tts_system *s, int inst, const double *in)
+{
+    const DevInstance &di = s->dinst[inst];
+    std::vector<R> x(di.n), y(di.n), z(di.n);
+    const std::vector<int64_t> &so = s->slot_of_atom[inst];
+    for (int64_t a = 0; a < di.n; ++a) {
+        const double vx = in[3 * a], vy = in[3 * a + 1], vz = in[3 * a + 2];
+        const double m = std::sqrt(vx * vx + vy * vy + vz * vz);
+        if (!(m > 0.0) || !std::isfinite(m)) return fail(TTS_ERR_ARG, "spin vectors must be finite and non-zero");
+        x[so[a]] = static_cast<R>(vx / m);
+        y[so[a]] = static_cast<R>(vy / m);
+        z[so[a]] = static_cast<R>(vz / m);
+    }
+    if (s->eng) {
+        int rc = engine_write_spins(s->eng, inst, x.data(), y.data(), z.data(), s->stream);
+        if (rc) return fail(rc, "engine spin write failed");
+        return TTS_OK;
+    }
+    const size_t off = di.slot_begin * sizeof(R);
+    TTS_CUDA(cudaMemcpyAsync(static_cast<char *>(s->b.sx) + off, x.data(), di.n * sizeof(R), cudaMemcpyHostToDevice, s->stream), "write spins");
+    TTS_CUDA(cudaMemcpyAsync(static_cast<char *>(s->b.sy) + off, y.data(), di.n * sizeof(R), cudaMemcpyHostToDevice, s->stream), "write spins");
+    TTS_CUDA(cudaMemcpyAsync(static_cast<char *>(s->b.sz) + off, z.data(), di.n * sizeof(R), cudaMemcpyHostToDevice, s->stream), "write spins");
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "write spins");
+    return TTS_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *tts_last_error(void) { return g_error.c_str(); }
+
+int tts_destroy(tts_system *s)
+{
+    if (!s) return TTS_OK;
+    cudaStreamSynchronize(s->stream);
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    drop_profile_events(s);
+    if (s->eng) engine_destroy(s->eng);
+    free_buffers(s);
+    if (s->capture) cudaStreamDestroy(s->capture);
+    delete s;
+    return TTS_OK;
+}
+
+int tts_create_system(const tts_system_desc *desc, void *stream, tts_system **out)
+{
+    if (!out) return fail(TTS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!desc) return fail(TTS_ERR_ARG, "desc is NULL");
+    int rc = validate(*desc);
+    if (rc) return rc;
+    tts_system *raw = new (std::nothrow) tts_system;
+    if (!raw) return fail(TTS_ERR_OOM, "host allocation failed");
+    // on any early return the partly built system is released with tts_destroy
+    struct Guard {
+        tts_system *p;
+        ~Guard() { if (p) tts_destroy(p); }
+        tts_system *operator->() const { return p; }
+        tts_system *get() const { return p; }
+        tts_system *release() { tts_system *q = p; p = nullptr; return q; }
+    } s{raw};
+    s->desc = *desc;
+    s->precision = desc->precision;
+    s->rsize = desc->precision == 64 ? 8 : 4;
+    s->stream = static_cast<cudaStream_t>(stream);
+    s->n_inst = desc->n_instances;
+    s->obs_capacity = desc->obs_capacity > 0 ? desc->obs_capacity : 1024;
+    // host build (all argument errors are found here, before any CUDA call)
+    s->host.resize(s->n_inst);
+    std::string err;
+    for (int i = 0; i < s->n_inst; ++i) {
+        rc = build_instance(*desc, i, &s->host[i], &err);
+        if (rc) return fail(rc, err);
+        if (s->host[i].ncolours > kMaxColours) return fail(TTS_ERR_UNSUPPORTED, "more than 16 colour classes");
+    }
+    // nothing from the caller's pointers is kept
+    s->desc.pos_explicit = nullptr;
+    s->desc.species_explicit = nullptr;
+    s->desc.inst_cells = nullptr;
+    s->desc.inst_frac1 = nullptr;
+    s->desc.inst_peak_Te = nullptr;
+    s->desc.inst_fwhm = nullptr;
+    if (desc->inst_peak_Te) s->inst_peak.assign(desc->inst_peak_Te, desc->inst_peak_Te + s->n_inst);
+    if (desc->inst_fwhm) s->inst_fwhm.assign(desc->inst_fwhm, desc->inst_fwhm + s->n_inst);
+
+    // slot layout: instance-major, colour-major inside, ascending atom id
+    s->slot_of_atom.resize(s->n_inst);
+    s->dinst.resize(s->n_inst);
+    int64_t slot = 0;
+    int obs_block = 0;
+    for (int i = 0; i < s->n_inst; ++i) {
+        HostInstance &hi = s->host[i];
+        DevInstance &di = s->dinst[i];
+        std::memset(&di, 0, sizeof di);
+        di.slot_begin = slot;
+        di.n = hi.n;
+        di.ncolours = hi.ncolours;
+        std::vector<int64_t> count(hi.ncolours + 1, 0);
+        for (int64_t a = 0; a < hi.n; ++a) count[hi.colour[a] + 1]++;
+        for (int c = 0; c < hi.ncolours; ++c) count[c + 1] += count[c];
+        for (int c = 0; c <= hi.ncolours; ++c) di.colour_begin[c] = count[c];
+        s->slot_of_atom[i].resize(hi.n);
+        std::vector<int64_t> next(count.begin(), count.end() - 1);
+        for (int64_t a = 0; a < hi.n; ++a) s->slot_of_atom[i][a] = next[hi.colour[a]]++;
+        di.cell_begin = i;
+        di.ncells = 1;
+        di.cells[0] = di.cells[1] = di.cells[2] = 1;
+        di.substeps = 1;
+        di.sigma_t = 1.0;
+        di.obs_block_begin = obs_block;
+        di.obs_block_count = static_cast<int>((hi.n + kObsBlock - 1) / kObsBlock);
+        obs_block += di.obs_block_count;
+        slot += hi.n;
+        s->max_colours = std::max(s->max_colours, hi.ncolours);
+        for (int64_t a = 0; a < hi.n; ++a)
+            s->zmax = std::max<int>(s->zmax, static_cast<int>(hi.nbr_begin[a + 1] - hi.nbr_begin[a]));
+    }
+    s->n_total = slot;
+    s->obs_blocks = obs_block;
+    s->max_passes = 2 * s->max_colours - 1;
+    if (s->n_total > 0x7fffffffLL) return fail(TTS_ERR_UNSUPPORTED, "more than 2^31 atoms in one system");
+
+    // pass ranges: pass p of an instance with K colours takes colour p for
+    // p < K-1 (h = dt/2), colour K-1 for p = K-1 (h = dt), colour 2K-2-p after
+    s->pass_offset.assign(s->max_passes + 1, 0);
+    s->pass_work.assign(s->max_passes, 0);
+    for (int pass = 0; pass < s->max_passes; ++pass) {
+        s->pass_offset[pass] = static_cast<int64_t>(s->ranges.size());
+        int64_t prefix = 0;
+        for (int i = 0; i < s->n_inst; ++i) {
+            const int K = s->dinst[i].ncolours;
+            if (pass >= 2 * K - 1) continue;
+            const int c = pass < K - 1 ? pass : (pass == K - 1 ? K - 1 : 2 * K - 2 - pass);
+            PassRange r;
+            r.slot_begin = s->dinst[i].slot_begin + s->dinst[i].colour_begin[c];
+            r.count = s->dinst[i].colour_begin[c + 1] - s->dinst[i].colour_begin[c];
+            r.prefix = prefix;
+            r.inst = i;
+            r.hsel = (pass == K - 1) ? 1 : 0;
+            if (r.count == 0) continue;
+            prefix += r.count;
+            s->ranges.push_back(r);
+        }
+        s->pass_work[pass] = prefix;
+    }
+    s->pass_offset[s->max_passes] = static_cast<int64_t>(s->ranges.size());
+
+    // step parameters
+    StepParams &p = s->p;
+    std::memset(&p, 0, sizeof p);
+    for (int t = 0; t < desc->nspecies; ++t) {
+        SpeciesParams &sp = p.sp[t];
+        sp.mu = desc->mu_muB[t] * kBohrMagneton;
+        sp.inv_mu = 1.0 / sp.mu;
+        sp.K = desc->K[t];
+        sp.kappa = 2.0 * desc->K[t] / sp.mu;
+        sp.alpha = desc->alpha[t];
+        sp.gprime = kGyro / (1.0 + sp.alpha * sp.alpha);
+    }
+    const double an = std::sqrt(desc->axis[0] * desc->axis[0] + desc->axis[1] * desc->axis[1] + desc->axis[2] * desc->axis[2]);
+    for (int k = 0; k < 3; ++k) {
+        p.axis[k] = an > 0.0 ? desc->axis[k] / an : 0.0;
+        p.B[k] = desc->B[k];
+    }
+    p.dt = desc->dt;
+    p.key0 = static_cast<uint32_t>(desc->seed & 0xffffffffu);
+    p.key1 = static_cast<uint32_t>(desc->seed >> 32);
+    p.nspecies = desc->nspecies;
+    p.n_total = s->n_total;
+    p.zmax = s->zmax;
+    p.n_instances = s->n_inst;
+    p.instance_base = desc->instance_base;
+    p.sample_every = desc->sample_every;
+    p.obs_capacity = s->obs_capacity;
+
+    // engine choice
+    s->engine = TTS_ENGINE_GENERAL;
+    if (desc->engine == TTS_ENGINE_CHECKER || desc->engine == TTS_ENGINE_RESIDENT ||
+        desc->engine == TTS_ENGINE_AUTO) {
+        const int want = desc->engine;
+        int chosen = engine_select(*desc, s->host, want);
+        if (chosen < 0) {
+            if (want != TTS_ENGINE_AUTO)
+                return fail(TTS_ERR_UNSUPPORTED, "the requested engine cannot run this system");
+        } else {
+            s->engine = chosen;
+        }
+    }
+
+    TTS_CUDA(cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking), "create capture stream");
+
+    // device buffers common to all engines
+    DevBuffers &b = s->b;
+    const int64_t N = s->n_total;
+    if ((rc = dev_alloc(&b.inst, s->n_inst, "instance table"))) return rc;
+    if ((rc = dev_alloc(&b.ranges, s->ranges.size(), "pass ranges"))) return rc;
+    if ((rc = dev_alloc(&b.step, 1, "step counter"))) return rc;
+    if ((rc = dev_alloc(&b.health, 1, "health word"))) return rc;
+    if ((rc = dev_alloc(&b.src_energy, s->n_inst, "source energy"))) return rc;
+    if ((rc = dev_alloc(&b.obs_partial, size_t(s->obs_blocks) * kObsFields, "observable partials"))) return rc;
+    if ((rc = dev_alloc(&b.obs_block_inst, s->obs_blocks, "observable blocks"))) return rc;
+    if ((rc = dev_alloc(&b.obs_block_begin, s->obs_blocks, "observable blocks"))) return rc;
+    if ((rc = dev_alloc(&b.obs_ring, size_t(s->n_inst) * s->obs_capacity * TTS_NOBS, "observable ring"))) return rc;
+    if ((rc = dev_alloc(&b.obs_count, s->n_inst, "observable counts"))) return rc;
+    if ((rc = dev_alloc(&b.obs_now, size_t(s->n_inst) * TTS_NOBS, "observable scratch"))) return rc;
+    char *q;
+    for (void **slotp : {&b.sx, &b.sy, &b.sz}) {
+        if ((rc = dev_alloc(&q, N * s->rsize, "spins"))) return rc;
+        *slotp = q;
+    }
+    if ((rc = dev_alloc(&b.atom, N, "atom ids"))) return rc;
+    if ((rc = dev_alloc(&b.species, N, "species"))) return rc;
+    if ((rc = dev_alloc(&b.cell, N, "cells"))) return rc;
+    // the neighbour table also serves the observable kernels of every engine
+    if ((rc = dev_alloc(&b.nbr, size_t(s->zmax) * N, "neighbour table"))) return rc;
+    if ((rc = dev_alloc(&q, size_t(s->zmax) * N * s->rsize, "coupling table"))) return rc;
+    b.nbr_w = q;
+    if ((rc = alloc_cells(s.get(), s->n_inst))) return rc;
+
+    // uploads
+    rc = s->precision == 64 ? upload_general<double>(s.get()) : upload_general<float>(s.get());
+    if (rc) return rc;
+    {
+        std::vector<int> bi(s->obs_blocks);
+        std::vector<int64_t> bb(s->obs_blocks);
+        for (int i = 0; i < s->n_inst; ++i)
+            for (int k = 0; k < s->dinst[i].obs_block_count; ++k) {
+                bi[s->dinst[i].obs_block_begin + k] = i;
+                bb[s->dinst[i].obs_block_begin + k] = s->dinst[i].slot_begin + int64_t(k) * kObsBlock;
+            }
+        if ((rc = upload(b.obs_block_inst, bi.data(), bi.size() * sizeof(int), s->stream, "upload obs blocks"))) return rc;
+        if ((rc = upload(b.obs_block_begin, bb.data(), bb.size() * sizeof(int64_t), s->stream, "upload obs blocks"))) return rc;
+    }
+    std::vector<double> Tb(s->n_inst, desc->T_bath), ones(s->n_inst, 1.0);
+    if ((rc = upload(b.Te, Tb.data(), Tb.size() * sizeof(double), s->stream, "upload bath"))) return rc;
+    if ((rc = upload(b.Tl, Tb.data(), Tb.size() * sizeof(double), s->stream, "upload bath"))) return rc;
+    if ((rc = upload(b.src_shape, ones.data(), ones.size() * sizeof(double), s->stream, "upload shape"))) return rc;
+    if ((rc = upload(b.inst, s->dinst.data(), s->dinst.size() * sizeof(DevInstance), s->stream, "upload instances"))) return rc;
+    if ((rc = upload(b.ranges, s->ranges.data(), s->ranges.size() * sizeof(PassRange), s->stream, "upload ranges"))) return rc;
+    TTS_CUDA(cudaMemsetAsync(b.step, 0, sizeof(int64_t), s->stream), "zero step");
+    TTS_CUDA(cudaMemsetAsync(b.health, 0, sizeof(unsigned), s->stream), "zero health");
+    TTS_CUDA(cudaMemsetAsync(b.src_energy, 0, s->n_inst * sizeof(double), s->stream), "zero energy");
+    TTS_CUDA(cudaMemsetAsync(b.obs_count, 0, s->n_inst * sizeof(int64_t), s->stream), "zero obs");
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "create");
+
+    if (s->engine != TTS_ENGINE_GENERAL) {
+        rc = engine_create(*desc, s->host, s->slot_of_atom, s->dinst, s->p, s->b, s->engine, s->stream, &s->eng);
+        if (rc) return fail(rc, std::string("engine set-up failed: ") + engine_last_error());
+    }
+    *out = s.release();
+    return TTS_OK;
+}
+
+int tts_set_ttm_grid(tts_system *s, const tts_ttm_desc *t)
+{
+    if (!s || !t) return fail(TTS_ERR_ARG, "null argument");
+    if (s->desc.lattice == TTS_LATTICE_CLUSTER) return fail(TTS_ERR_UNSUPPORTED, "TTM grids need a periodic lattice");
+    for (int k = 0; k < 3; ++k)
+        if (t->cells[k] < 1) return fail(TTS_ERR_ARG, "TTM cell counts must be >= 1");
+    if (!(t->gamma_e > 0.0) || !(t->C_l > 0.0) || !(t->G >= 0.0) || !(t->kappa_e >= 0.0) || !(t->T0 > 0.0))
+        return fail(TTS_ERR_ARG, "TTM coefficients out of range");
+    if (t->source < 0 || t->source > 2 || t->spatial < 0 || t->spatial > 2) return fail(TTS_ERR_ARG, "bad TTM mode");
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "set ttm");
+    const int nc = t->cells[0] * t->cells[1] * t->cells[2];
+    const int total = nc * s->n_inst;
+    int rc = alloc_cells(s, total);
+    if (rc) return rc;
+    std::vector<double> shape(total), Te(total, t->T0);
+    std::vector<int> cellmap(s->n_total);
+    s->P0.assign(s->n_inst, t->P0);
+    // calibrations shared by instances with equal box, grid and pulse
+    struct Cal { double box[3], peak, fwhm, P0; };
+    std::vector<Cal> cache;
+    for (int i = 0; i < s->n_inst; ++i) {
+        const HostInstance &hi = s->host[i];
+        DevInstance &di = s->dinst[i];
+        const double my_fwhm = s->inst_fwhm.empty() ? t->fwhm : s->inst_fwhm[i];
+        const double my_peak = s->inst_peak.empty() ? t->peak_Te : s->inst_peak[i];
+        if (t->source != TTS_SOURCE_NONE && !(my_fwhm > 0.0)) return fail(TTS_ERR_ARG, "pulse FWHM must be positive");
+        HostTtm h;
+        make_host_ttm(s->desc, hi, *t, my_fwhm, &h);
+        double P0 = t->P0;
+        if (t->source == TTS_SOURCE_PEAK) {
+            if (!(my_peak > t->T0)) return fail(TTS_ERR_ARG, "peak T_e must exceed T0");
+            bool hit = false;
+            for (const Cal &c : cache)
+                if (c.box[0] == hi.box[0] && c.box[1] == hi.box[1] && c.box[2] == hi.box[2] && c.peak == my_peak &&
+                    c.fwhm == my_fwhm) {
+                    P0 = c.P0;
+                    hit = true;
+                    break;
+                }
+            if (!hit) {
+                P0 = calibrate_P0(s->desc, *t, h, my_peak);
+                cache.push_back({{hi.box[0], hi.box[1], hi.box[2]}, my_peak, my_fwhm, P0});
+            }
+        }
+        s->P0[i] = P0;
+        di.cell_begin = i * nc;
+        di.ncells = nc;
+        for (int k = 0; k < 3; ++k) {
+            di.cells[k] = t->cells[k];
+            di.dx[k] = h.dx[k];
+        }
+        di.cell_volume = h.vol;
+        di.substeps = h.substeps;
+        di.P0 = P0;
+        di.sigma_t = h.sigma_t;
+        di.t0 = h.t0;
+        for (int c = 0; c < nc; ++c) shape[di.cell_begin + c] = h.shape[c];
+        // cell of each atom: floor(x / L * n) on the exact half-lattice coordinate
+        for (int64_t a = 0; a < hi.n; ++a) {
+            int cc[3];
+            for (int k = 0; k < 3; ++k)
+                cc[k] = static_cast<int>((int64_t(hi.half[3 * a + k]) * t->cells[k]) / (2LL * hi.cells[k]));
+            cellmap[di.slot_begin + s->slot_of_atom[i][a]] = di.cell_begin + (cc[2] * t->cells[1] + cc[1]) * t->cells[0] + cc[0];
+        }
+    }
+    DevBuffers &b = s->b;
+    if ((rc = upload(b.Te, Te.data(), total * sizeof(double), s->stream, "upload T_e"))) return rc;
+    if ((rc = upload(b.Tl, Te.data(), total * sizeof(double), s->stream, "upload T_l"))) return rc;
+    if ((rc = upload(b.src_shape, shape.data(), total * sizeof(double), s->stream, "upload shape"))) return rc;
+    if ((rc = upload(b.cell, cellmap.data(), cellmap.size() * sizeof(int), s->stream, "upload cell map"))) return rc;
+    if ((rc = upload(b.inst, s->dinst.data(), s->dinst.size() * sizeof(DevInstance), s->stream, "upload instances"))) return rc;
+    TTS_CUDA(cudaMemsetAsync(b.src_energy, 0, s->n_inst * sizeof(double), s->stream), "zero energy");
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "set ttm");
+    s->tp.active = 1;
+    s->tp.gamma_e = t->gamma_e;
+    s->tp.C_l = t->C_l;
+    s->tp.G = t->G;
+    s->tp.kappa_e = t->kappa_e;
+    s->tp.T0 = t->T0;
+    s->tp.source = t->source;
+    s->tp.spatial = t->spatial;
+    s->tp.sigma_xy = t->sigma_xy;
+    s->tp.depth_z = t->depth_z;
+    s->ttm_active = true;
+    if (s->eng) {
+        rc = engine_set_cells(s->eng, s->dinst, cellmap, s->stream);
+        if (rc) return fail(rc, std::string("engine TTM set-up failed: ") + engine_last_error());
+    }
+    s->dirty = true;
+    return TTS_OK;
+}
+
+int tts_step(tts_system *s, int64_t nsteps)
+{
+    if (!s) return fail(TTS_ERR_ARG, "null system");
+    if (nsteps < 0) return fail(TTS_ERR_ARG, "nsteps must be >= 0");
+    if (nsteps == 0) return TTS_OK;
+    if (s->profiling) {
+        for (int64_t i = 0; i < nsteps; ++i) {
+            cudaEvent_t ev[2];
+            TTS_CUDA(cudaEventCreate(&ev[0]), "profile event");
+            TTS_CUDA(cudaEventCreate(&ev[1]), "profile event");
+            s->prof_events.push_back(ev[0]);
+            s->prof_events.push_back(ev[1]);
+            int kernels = 0;
+            cudaError_t e = record_step(s, s->stream, &kernels, ev[0], ev[1]);
+            if (e != cudaSuccess) return cuda_fail(e, "profiled step");
+            s->launches += kernels;
+        }
+        return TTS_OK;
+    }
+    if (s->dirty) {
+        int rc = build_graph(s);
+        if (rc) return rc;
+    }
+    for (int64_t i = 0; i < nsteps; ++i) TTS_CUDA(cudaGraphLaunch(s->graph, s->stream), "launch step graph");
+    s->launches += nsteps * s->kernels_per_step;
+    return TTS_OK;
+}
+
+int tts_profile_enable(tts_system *s, int enable)
+{
+    if (!s) return fail(TTS_ERR_ARG, "null system");
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "profile enable");
+    drop_profile_events(s);
+    s->prof_ms = 0.0;
+    s->prof_steps = 0;
+    s->profiling = enable != 0;
+    return TTS_OK;
+}
+
+int tts_profile_read(tts_system *s, double *ms, int64_t *steps, int64_t *spin_steps)
+{
+    if (!s) return fail(TTS_ERR_ARG, "null system");
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "profile read");
+    for (size_t k = 0; k + 1 < s->prof_events.size(); k += 2) {
+        float t = 0.0f;
+        TTS_CUDA(cudaEventElapsedTime(&t, s->prof_events[k], s->prof_events[k + 1]), "profile elapsed");
+        s->prof_ms += t;
+        s->prof_steps += 1;
+    }
+    drop_profile_events(s);
+    if (ms) *ms = s->prof_ms;
+    if (steps) *steps = s->prof_steps;
+    if (spin_steps) *spin_steps = s->prof_steps * s->n_total;
+    return TTS_OK;
+}
+
+int tts_sync(tts_system *s)
+{
+    if (!s) return fail(TTS_ERR_ARG, "null system");
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "synchronise");
+    unsigned h = 0;
+    TTS_CUDA(cudaMemcpy(&h, s->b.health, sizeof h, cudaMemcpyDeviceToHost), "read health");
+    if (h & kHealthTimeout) return fail(TTS_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out");
+    if (h & kHealthNonFinite) return fail(TTS_ERR_HEALTH, "non-finite spin produced on the device");
+    return TTS_OK;
+}
+
+int tts_observables(tts_system *s, int inst, double *out, int64_t max_samples, int64_t *n_written)
+{
+    int rc = check_inst(s, inst);
+    if (rc) return rc;
+    if (!out || !n_written || max_samples < 0) return fail(TTS_ERR_ARG, "bad output arguments");
+    if ((rc = tts_sync(s))) return rc;
+    int64_t count = 0;
+    TTS_CUDA(cudaMemcpy(&count, s->b.obs_count + inst, sizeof count, cudaMemcpyDeviceToHost), "read obs count");
+    const int64_t cap = s->obs_capacity;
+    const int64_t have = std::min(count, cap);
+    std::vector<double> ring(size_t(cap) * TTS_NOBS);
+    TTS_CUDA(cudaMemcpy(ring.data(), s->b.obs_ring + size_t(inst) * cap * TTS_NOBS, ring.size() * sizeof(double),
+                        cudaMemcpyDeviceToHost), "read obs ring");
+    const int64_t first = count - have;
+    const int64_t m = std::min(have, max_samples);
+    for (int64_t k = 0; k < m; ++k) {
+        const int64_t src = (first + k) % cap;
+        std::memcpy(out + k * TTS_NOBS, ring.data() + src * TTS_NOBS, TTS_NOBS * sizeof(double));
+    }
+    *n_written = m;
+    return TTS_OK;
+}
+
+int tts_observe_now(tts_system *s, int inst, double *out)
+{
+    int rc = check_inst(s, inst);
+    if (rc) return rc;
+    if (!out) return fail(TTS_ERR_ARG, "null output");
+    if (s->eng) {
+        cudaError_t e = engine_sync_to_general(s->eng, s->b, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "engine gather");
+    }
+    cudaError_t e = launch_obs(s->p, s->b, s->precision, s->obs_blocks, 1, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "observe");
+    s->launches += 2;
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "observe");
+    TTS_CUDA(cudaMemcpy(out, s->b.obs_now + size_t(inst) * TTS_NOBS, TTS_NOBS * sizeof(double), cudaMemcpyDeviceToHost),
+             "read observation");
+    return TTS_OK;
+}
+
+int tts_get_spins(tts_system *s, int inst, double *xyz)
+{
+    int rc = check_inst(s, inst);
+    if (rc) return rc;
+    if (!xyz) return fail(TTS_ERR_ARG, "null output");
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "get spins");
+    return s->precision == 64 ? read_instance_spins<double>(s, inst, xyz) : read_instance_spins<float>(s, inst, xyz);
+}
+
+int tts_set_spins(tts_system *s, int inst, const double *xyz)
+{
+    int rc = check_inst(s, inst);
+    if (rc) return rc;
+    if (!xyz) return fail(TTS_ERR_ARG, "null input");
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "set spins");
+    return s->precision == 64 ? write_instance_spins<double>(s, inst, xyz) : write_instance_spins<float>(s, inst, xyz);
+}
+
+int tts_get_all_spins(tts_system *s, double *xyz)
+{
+    if (!s || !xyz) return fail(TTS_ERR_ARG, "null argument");
+    for (int i = 0; i < s->n_inst; ++i) {
+        int rc = tts_get_spins(s, i, xyz);
+        if (rc) return rc;
+        xyz += 3 * s->dinst[i].n;
+    }
+    return TTS_OK;
+}
+
+int tts_set_all_spins(tts_system *s, const double *xyz)
+{
+    if (!s || !xyz) return fail(TTS_ERR_ARG, "null argument");
+    for (int i = 0; i < s->n_inst; ++i) {
+        int rc = tts_set_spins(s, i, xyz);
+        if (rc) return rc;
+        xyz += 3 * s->dinst[i].n;
+    }
+    return TTS_OK;
+}
+
+int tts_instance_size(tts_system *s, int inst, int64_t *n, int *ncol)
+{
+    int rc = check_inst(s, inst);
+    if (rc) return rc;
+    if (n) *n = s->dinst[inst].n;
+    if (ncol) *ncol = s->dinst[inst].ncolours;
+    return TTS_OK;
+}
+
+int tts_get_species(tts_system *s, int inst, int *out)
+{
+    int rc = check_inst(s, inst);
+    if (rc) return rc;
+    if (!out) return fail(TTS_ERR_ARG, "null output");
+    for (int64_t a = 0; a < s->dinst[inst].n; ++a) out[a] = s->host[inst].species[a];
+    return TTS_OK;
+}
+
+int tts_get_colours(tts_system *s, int inst, int *out)
+{
+    int rc = check_inst(s, inst);
+    if (rc) return rc;
+    if (!out) return fail(TTS_ERR_ARG, "null output");
+    for (int64_t a = 0; a < s->dinst[inst].n; ++a) out[a] = s->host[inst].colour[a];
+    return TTS_OK;
+}
+
+int tts_get_ttm(tts_system *s, int inst, double *Te, double *Tl, double *P0)
+{
+    int rc = check_inst(s, inst);
+    if (rc) return rc;
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "get ttm");
+    const DevInstance &di = s->dinst[inst];
+    if (Te) TTS_CUDA(cudaMemcpy(Te, s->b.Te + di.cell_begin, di.ncells * sizeof(double), cudaMemcpyDeviceToHost), "read T_e");
+    if (Tl) TTS_CUDA(cudaMemcpy(Tl, s->b.Tl + di.cell_begin, di.ncells * sizeof(double), cudaMemcpyDeviceToHost), "read T_l");
+    if (P0) *P0 = s->ttm_active ? s->P0[inst] : 0.0;
+    return TTS_OK;
+}
+
+int tts_set_ttm_state(tts_system *s, int inst, const double *Te, const double *Tl)
+{
+    int rc = check_inst(s, inst);
+    if (rc) return rc;
+    if (!s->ttm_active) return fail(TTS_ERR_STATE, "no TTM grid set");
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "set ttm state");
+    const DevInstance &di = s->dinst[inst];
+    if (Te) TTS_CUDA(cudaMemcpy(s->b.Te + di.cell_begin, Te, di.ncells * sizeof(double), cudaMemcpyHostToDevice), "write T_e");
+    if (Tl) TTS_CUDA(cudaMemcpy(s->b.Tl + di.cell_begin, Tl, di.ncells * sizeof(double), cudaMemcpyHostToDevice), "write T_l");
+    return TTS_OK;
+}
+
+int tts_get_step(tts_system *s, int64_t *step)
+{
+    if (!s || !step) return fail(TTS_ERR_ARG, "null argument");
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "get step");
+    TTS_CUDA(cudaMemcpy(step, s->b.step, sizeof(int64_t), cudaMemcpyDeviceToHost), "read step");
+    return TTS_OK;
+}
+
+int tts_set_step(tts_system *s, int64_t step)
+{
+    if (!s || step < 0) return fail(TTS_ERR_ARG, "bad argument");
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "set step");
+    TTS_CUDA(cudaMemcpy(s->b.step, &step, sizeof(int64_t), cudaMemcpyHostToDevice), "write step");
+    return TTS_OK;
+}
+
+int tts_info(tts_system *s, tts_info_t *info)
+{
+    if (!s || !info) return fail(TTS_ERR_ARG, "null argument");
+    info->n_total = s->n_total;
+    info->n_instances = s->n_inst;
+    info->engine = s->engine;
+    info->precision = s->precision;
+    info->max_colours = s->max_colours;
+    int64_t st = 0;
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "info");
+    TTS_CUDA(cudaMemcpy(&st, s->b.step, sizeof st, cudaMemcpyDeviceToHost), "read step");
+    info->steps_done = st;
+    info->kernel_launches = s->launches;
+    return TTS_OK;
+}
+
+// Checkpoint layout: header {magic, version, precision, n_total, n_inst,
+// ncells_total, obs_capacity}, step, then spins (slot order, 3 arrays),
+// T_e, T_l, source energies, observable counts and rings.
+int tts_get_state(tts_system *s, void *buf, size_t *nbytes)
+{
+    if (!s || !nbytes) return fail(TTS_ERR_ARG, "null argument");
+    const size_t hdr = 8 * sizeof(int64_t);
+    const size_t spin = 3 * size_t(s->n_total) * s->rsize;
+    const size_t cells = 2 * size_t(s->ncells_total) * sizeof(double);
+    const size_t en = s->n_inst * sizeof(double);
+    const size_t oc = s->n_inst * sizeof(int64_t);
+    const size_t ring = size_t(s->n_inst) * s->obs_capacity * TTS_NOBS * sizeof(double);
+    const size_t need = hdr + spin + cells + en + oc + ring;
+    if (!buf) {
+        *nbytes = need;
+        return TTS_OK;
+    }
+    if (*nbytes < need) return fail(TTS_ERR_ARG, "state buffer too small");
+    if (s->eng) {
+        cudaError_t e = engine_sync_to_general(s->eng, s->b, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "engine gather");
+    }
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "get state");
+    char *o = static_cast<char *>(buf);
+    int64_t h[8] = {0x7474735354415445LL, 1, s->precision, s->n_total, s->n_inst, s->ncells_total, s->obs_capacity, 0};
+    TTS_CUDA(cudaMemcpy(&h[7], s->b.step, sizeof(int64_t), cudaMemcpyDeviceToHost), "read step");
+    std::memcpy(o, h, hdr);
+    o += hdr;
+    for (void *arr : {s->b.sx, s->b.sy, s->b.sz}) {
+        TTS_CUDA(cudaMemcpy(o, arr, size_t(s->n_total) * s->rsize, cudaMemcpyDeviceToHost), "read spins");
+        o += size_t(s->n_total) * s->rsize;
+    }
+    TTS_CUDA(cudaMemcpy(o, s->b.Te, s->ncells_total * sizeof(double), cudaMemcpyDeviceToHost), "read T_e");
+    o += s->ncells_total * sizeof(double);
+    TTS_CUDA(cudaMemcpy(o, s->b.Tl, s->ncells_total * sizeof(double), cudaMemcpyDeviceToHost), "read T_l");
+    o += s->ncells_total * sizeof(double);
+    TTS_CUDA(cudaMemcpy(o, s->b.src_energy, en, cudaMemcpyDeviceToHost), "read energies");
+    o += en;
+    TTS_CUDA(cudaMemcpy(o, s->b.obs_count, oc, cudaMemcpyDeviceToHost), "read counts");
+    o += oc;
+    TTS_CUDA(cudaMemcpy(o, s->b.obs_ring, ring, cudaMemcpyDeviceToHost), "read ring");
+    *nbytes = need;
+    return TTS_OK;
+}
+
+int tts_set_state(tts_system *s, const void *buf, size_t nbytes)
+{
+    if (!s || !buf) return fail(TTS_ERR_ARG, "null argument");
+    size_t need = 0;
+    tts_get_state(s, nullptr, &need);
+    if (nbytes != need) return fail(TTS_ERR_ARG, "state size does not match this system");
+    const char *o = static_cast<const char *>(buf);
+    int64_t h[8];
+    std::memcpy(h, o, sizeof h);
+    if (h[0] != 0x7474735354415445LL || h[1] != 1 || h[2] != s->precision || h[3] != s->n_total ||
+        h[4] != s->n_inst || h[5] != s->ncells_total || h[6] != s->obs_capacity)
+        return fail(TTS_ERR_ARG, "state was taken from a different system layout");
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "set state");
+    o += sizeof h;
+    TTS_CUDA(cudaMemcpy(s->b.step, &h[7], sizeof(int64_t), cudaMemcpyHostToDevice), "write step");
+    for (void *arr : {s->b.sx, s->b.sy, s->b.sz}) {
+        TTS_CUDA(cudaMemcpy(arr, o, size_t(s->n_total) * s->rsize, cudaMemcpyHostToDevice), "write spins");
+        o += size_t(s->n_total) * s->rsize;
+    }
+    TTS_CUDA(cudaMemcpy(s->b.Te, o, s->ncells_total * sizeof(double), cudaMemcpyHostToDevice), "write T_e");
+    o += s->ncells_total * sizeof(double);
+    TTS_CUDA(cudaMemcpy(s->b.Tl, o, s->ncells_total * sizeof(double), cudaMemcpyHostToDevice), "write T_l");
+    o += s->ncells_total * sizeof(double);
+    TTS_CUDA(cudaMemcpy(s->b.src_energy, o, s->n_inst * sizeof(double), cudaMemcpyHostToDevice), "write energies");
+    o += s->n_inst * sizeof(double);
+    TTS_CUDA(cudaMemcpy(s->b.obs_count, o, s->n_inst * sizeof(int64_t), cudaMemcpyHostToDevice), "write counts");
+    o += s->n_inst * sizeof(int64_t);
+    TTS_CUDA(cudaMemcpy(s->b.obs_ring, o, size_t(s->n_inst) * s->obs_capacity * TTS_NOBS * sizeof(double),
+                        cudaMemcpyHostToDevice), "write ring");
+    if (s->eng) {
+        cudaError_t e = engine_sync_from_general(s->eng, s->b, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "engine scatter");
+    }
+    return TTS_OK;
+}
+
+}  // extern "C"
