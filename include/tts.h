@@ -244,6 +244,35 @@ TTS_API int tts_profile_enable(tts_system *sys, int enable);
  * (atoms x steps).  Synchronises the stream. */
 TTS_API int tts_profile_read(tts_system *sys, double *ms, int64_t *steps, int64_t *spin_steps);
 
+/* Largest grid (cells) that tts_ttm_advance_noalloc() accepts. */
+#define TTS_NOALLOC_MAX_CELLS 65536
+
+/* Advance one two-temperature grid held in the caller's device buffers by
+ * one time step dt (from t = step * dt), without allocating any memory.
+ * The paper has no counterpart: this is a convenience for callers that cannot
+ * allocate device memory, such as code whose device memory is entirely owned
+ * by another allocator (a framework's caching pool) or latency-critical code
+ * that must not call cudaMalloc / cudaFree, which can synchronise the device.
+ * The update is that of tts_step's TTM grid (explicit FTCS of the electron
+ * energy, periodic Laplacian, e-ph exchange, Gaussian source with the spatial
+ * profile of `t`), except that no calibration is done: the source power is
+ * t->P0 for any source kind other than TTS_SOURCE_NONE, with pulse width
+ * t->fwhm.  box_ang: grid box edges in angstrom.  dev_Te, dev_Tl: device
+ * arrays of t->cells[0]*t->cells[1]*t->cells[2] doubles (x fastest), updated
+ * in place.  dev_deposited: NULL or one device double that receives the
+ * source energy (J) deposited by this call.  stream: cudaStream_t or NULL.
+ * Scratch lives in a fixed device array of TTS_NOALLOC_MAX_CELLS doubles
+ * (512 KiB) that every GPU loading this library holds until the process
+ * exits; larger grids are rejected with TTS_ERR_ARG.  The first call on each
+ * device looks the array's device address up (cudaGetSymbolAddress), so make
+ * that first call before any stream capture.  All calls on one GPU share that
+ * GPU's array and find in it whatever the previous call left (nothing has to
+ * start at zero): calls that overlap on the same GPU, for example on two
+ * streams, race on it and give wrong results.  Asynchronous: returns once queued.
+ * Errors: TTS_ERR_ARG, TTS_ERR_CUDA, TTS_ERR_UNSUPPORTED (device index > 63). */
+TTS_API int tts_ttm_advance_noalloc(const tts_ttm_desc *t, const double box_ang[3], double dt, int64_t step,
+                                    double *dev_Te, double *dev_Tl, double *dev_deposited, void *stream);
+
 /* Message of the calling thread's last failed call (never NULL). */
 TTS_API const char *tts_last_error(void);
 

@@ -98,6 +98,8 @@ _SIG = {
     "tts_info": [C.c_void_p, _P(tts_info_t)],
     "tts_profile_enable": [C.c_void_p, C.c_int],
     "tts_profile_read": [C.c_void_p, _P(C.c_double), _P(C.c_int64), _P(C.c_int64)],
+    "tts_ttm_advance_noalloc": [_P(tts_ttm_desc), _P(C.c_double), C.c_double, C.c_int64, C.c_void_p,
+                                C.c_void_p, C.c_void_p, C.c_void_p],
 }
 
 _LIB = None
@@ -349,6 +351,17 @@ class System:
         ss = C.c_int64()
         _check(load().tts_profile_read(self._h, C.byref(ms), C.byref(st), C.byref(ss)))
         return ms.value, st.value, ss.value
+
+
+def ttm_advance_noalloc(ttm, box_ang, dt, step, dev_Te, dev_Tl, dev_deposited=0, stream=0):
+    """tts_ttm_advance_noalloc: one TTM step on caller-owned device buffers
+    (device addresses as ints), allocating nothing.  ttm["P0"] is the source
+    power used as given."""
+    t = make_ttm(ttm)
+    box = (C.c_double * 3)(*[float(v) for v in box_ang])
+    _check(load().tts_ttm_advance_noalloc(C.byref(t), box, float(dt), int(step), C.c_void_p(dev_Te),
+                                          C.c_void_p(dev_Tl), C.c_void_p(dev_deposited or 0),
+                                          C.c_void_p(stream or 0)))
 
 
 def create_system(sysd, ttm=None, precision=64, engine="auto", stream=None, obs_capacity=0,

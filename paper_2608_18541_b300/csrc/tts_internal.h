@@ -40,6 +40,9 @@ int build_instance(const tts_system_desc &d, int inst, HostInstance *out, std::s
 // Colour-class rule check / greedy colouring (exposed for the resident engine).
 void colour_instance(const tts_system_desc &d, HostInstance *hi);
 
+// Message returned by tts_last_error() for the calling thread.
+void set_last_error(const std::string &msg);
+
 // ---------------------------------------------------------------------------
 // Device-side tables (plain structs copied to device memory).
 // ---------------------------------------------------------------------------

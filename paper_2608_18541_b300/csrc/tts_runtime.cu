@@ -40,6 +40,8 @@ int cuda_fail(cudaError_t e, const char *what)
 
 }  // namespace
 
+void tts::set_last_error(const std::string &msg) { g_error = msg; }
+
 struct tts_system {
     tts_system_desc desc{};
     int precision = 32;
