@@ -128,6 +128,48 @@ def _traffic(kernel, precision):
     return e["bytes_per_launch"] if h == e.get("source_sha") else None
 
 
+def ensemble_leg(P, W, stream, steps=200, sample=8):
+    """Batched FP32 ensemble (1024 GdFeCo instances of uneven size in one
+    persistent launch per call) against the plain FP64 path that advances one
+    instance per launch sequence, on the same GPU."""
+    import torch
+
+    sysd, ttm = W.config_ensemble()
+    g = P.System(sysd, ttm, precision=32, engine="auto", stream=stream.cuda_stream)
+    g.step(5)
+    g.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batched = g.n_total * steps / (e0.elapsed_time(e1) / 1e3)
+    engine = g.engine
+    del g
+    # FP64, one instance per system, instances advanced one after another
+    picks = list(range(0, len(sysd["instances"]), len(sysd["instances"]) // sample))[:sample]
+    spins, ms = 0, 0.0
+    for k in picks:
+        one = dict(sysd, instances=[sysd["instances"][k]])
+        g1 = P.System(one, ttm, precision=64, engine="general", stream=stream.cuda_stream, instance_base=k)
+        g1.step(2)
+        g1.sync()
+        e0.record(stream)
+        g1.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        spins += g1.n_total
+        del g1
+    fp64 = spins * steps / (ms / 1e3)
+    return {"workload": "GdFeCo ensemble, 8 peak T_e x 8 FWHM x 16 realisations = 1024 instances, "
+                        "L ~ U{12..24}, x ~ U[0.2, 0.3], one-cell 2TM each",
+            "batched_fp32": batched, "batched_engine": engine,
+            "fp64_one_instance_per_launch": fp64, "fp64_sample": "%d instances, %d steps each" % (len(picks), steps),
+            "ratio": batched / fp64, "unit": "spin-steps/s"}
+
+
 def cpu_oracle_rate(sysd, ttm, steps):
     """Time the FP64 CPU oracle (single thread) on one realisation."""
     import oracle as O
@@ -184,6 +226,7 @@ def main():
     ap.add_argument("--engine", default="auto")
     ap.add_argument("--cpu-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     args = ap.parse_args()
 
     world = _env_int("WORLD_SIZE", 1)
@@ -285,6 +328,10 @@ def main():
                 "traffic": _traffic(kernel_name, args.precision), "kernel": kernel_name,
                 "bytes_per_unit": bpu, "units_per_launch": spins,
                 "avg_launch_ms": kern_ms / max(kern_steps, 1)}
+    ens = None
+    if world == 1 and not args.no_ensemble:
+        from paper_2608_18541_b300 import workloads as W
+        ens = ensemble_leg(P, W, stream)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         rate, n1, secs = cpu_oracle_rate(sysd, ttm, args.cpu_steps)
@@ -300,7 +347,7 @@ def main():
                    "engine": g.engine, "l2": "state and tables exceed L2 (126 MB) per step" if spins * 16 > 126e6
                    else "working set may fit L2", "parallelism": "instances sharded, dp%d" % world},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-        "clocks": clocks,
+        "clocks": clocks, "ensemble": ens,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -147,6 +147,33 @@ typedef struct {
 
 typedef struct tts_system tts_system;
 
+/* Moving lattice (paper Sec. II.A): atoms move under a pair potential plus
+ * the exchange-mediated force -dJ(r_ij)/dr (s_i.s_j), advanced together with
+ * the spins.  One lattice step of length spin_substeps * dt is
+ *   v += F dtL/2M; spin_substeps/2 spin steps; x += v dtL; J(r_ij) refreshed;
+ *   spin_substeps/2 spin steps; F recomputed; v += F dtL/2M;
+ *   electron-ion coupling (exact Ornstein-Uhlenbeck update of the friction
+ *   -gamma_p v plus noise at the atom's T_e, the kinetic-energy change taken
+ *   from the electrons of its TTM cell); TTM grid advanced by dtL.
+ * The pair potential is Morse in shifted-force form (energy and force vanish
+ * at morse_rc).  Candidate pairs are those within max(cutoffs) + skin of the
+ * reference lattice; an atom that moves further than skin/2 from its site
+ * sets the health word (TTS_ERR_HEALTH at tts_sync). */
+typedef struct {
+    double mass_amu;
+    double morse_D;       /* J */
+    double morse_alpha;   /* 1/angstrom */
+    double morse_r0;      /* angstrom */
+    double morse_rc;      /* angstrom */
+    int spin_substeps;    /* spin steps per lattice step, even */
+    double strain_amp;    /* initial u_z = A Lz / (2 pi) sin(2 pi z / Lz) */
+    double T_init;        /* initial ion temperature (Maxwell-Boltzmann, Philox
+                             counter (atom, 0, 0xFFFF0003, instance)), K */
+    double gamma_p;       /* electron-ion friction, kg/s (0 = none); noise from
+                             Philox counter (atom, lattice step, 0xFFFF0002, instance) */
+    double skin;          /* angstrom */
+} tts_lattice_desc;
+
 /* Facts about a created system. */
 typedef struct {
     int64_t n_total;        /* atoms over all instances */
@@ -220,6 +247,18 @@ TTS_API int tts_get_colours(tts_system *sys, int inst, int *host_colours);
 /* T_e, T_l of an instance's grid cells (x fastest) and its source power P0. */
 TTS_API int tts_get_ttm(tts_system *sys, int inst, double *host_Te, double *host_Tl, double *P0);
 TTS_API int tts_set_ttm_state(tts_system *sys, int inst, const double *host_Te, const double *host_Tl);
+
+/* Switch on the moving lattice (before tts_set_ttm_grid; general engine only).
+ * From then on tts_step(n) advances n lattice steps and observables are
+ * sampled every sample_every lattice steps, with [16] the ion kinetic
+ * temperature, [17] the kinetic and [18] the pair-potential energy.
+ * Errors: TTS_ERR_ARG, TTS_ERR_STATE (TTM grid already set),
+ * TTS_ERR_UNSUPPORTED (cluster or a fast engine). */
+TTS_API int tts_set_lattice(tts_system *sys, const tts_lattice_desc *lat);
+/* Positions (angstrom, wrapped into the box) and velocities (m/s) of one
+ * instance, canonical order. */
+TTS_API int tts_get_positions(tts_system *sys, int inst, double *host_xyz);
+TTS_API int tts_get_velocities(tts_system *sys, int inst, double *host_xyz);
 
 /* The step counter (the Philox step word and the time t = step * dt). */
 TTS_API int tts_get_step(tts_system *sys, int64_t *step);

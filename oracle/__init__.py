@@ -45,6 +45,14 @@ class _Ttm(C.Structure):
     ]
 
 
+class _Lattice(C.Structure):
+    _fields_ = [
+        ("mass_amu", C.c_double), ("morse_D", C.c_double), ("morse_alpha", C.c_double),
+        ("morse_r0", C.c_double), ("morse_rc", C.c_double), ("spin_substeps", C.c_int),
+        ("strain_amp", C.c_double), ("T_init", C.c_double), ("gamma_p", C.c_double),
+    ]
+
+
 _LATTICE = {"sc": 0, "bcc": 1, "fcc": 2, "cluster": 3}
 _EXKIND = {"none": 0, "const": 1, "bethe_slater": 2}
 _SOURCE = {"none": 0, "peak": 1, "power": 2}
@@ -96,6 +104,16 @@ def lib():
         L.orc_ttm_source_energy.argtypes = [C.c_void_p]
         L.orc_ttm_source_energy.restype = d
         L.orc_atom_cell.argtypes = [C.c_void_p, C.c_int]
+        L.orc_set_lattice.argtypes = [C.c_void_p, P(_Lattice), C.c_char_p, C.c_int]
+        L.orc_lattice_step.argtypes = [C.c_void_p, i64]
+        L.orc_lattice_stepcount.argtypes = [C.c_void_p]
+        L.orc_lattice_stepcount.restype = i64
+        for name in ("orc_get_velocities", "orc_set_positions", "orc_set_velocities", "orc_get_forces"):
+            getattr(L, name).argtypes = [C.c_void_p, P(d)]
+        L.orc_lattice_energy.argtypes = [C.c_void_p, P(d), P(d)]
+        L.orc_colour_violations.argtypes = [C.c_void_p]
+        L.orc_ion_energy_to_electrons.argtypes = [C.c_void_p]
+        L.orc_ion_energy_to_electrons.restype = d
         _LIB = L
     return _LIB
 
@@ -158,10 +176,10 @@ def flow(s, B, alpha, h):
 # ---------------------------------------------------------------------------
 # system
 # ---------------------------------------------------------------------------
-def _fill_params(sysd, instance, noise_mu_power):
+def _fill_params(sysd, instance, index, noise_mu_power):
     p = _Params()
     inst = sysd.get("instances")
-    over = inst[instance] if inst else {}
+    over = inst[index] if inst else {}
     p.lattice = _LATTICE[sysd["lattice"]]
     p.nx = int(over.get("nx", sysd.get("nx", 1)))
     p.ny = int(over.get("ny", sysd.get("ny", 1)))
@@ -226,20 +244,31 @@ def _fill_ttm(t, over):
 
 
 class Oracle:
-    """One instance (realisation) of a system description, advanced on the CPU."""
+    """One instance (realisation) of a system description, advanced on the CPU.
 
-    def __init__(self, sysd, ttm=None, instance=0, noise_mu_power=0.5):
+    instance: the realisation id that keys the noise and the alloy placement;
+    index: the entry of sysd["instances"] that gives its size, composition and
+    pulse (defaults to `instance`)."""
+
+    def __init__(self, sysd, ttm=None, instance=0, noise_mu_power=0.5, index=None, lattice=None):
         L = lib()
-        p, self._keep = _fill_params(sysd, instance, noise_mu_power)
+        index = instance if index is None else index
+        p, self._keep = _fill_params(sysd, instance, index, noise_mu_power)
         err = C.create_string_buffer(256)
         h = L.orc_create(C.byref(p), err, 256)
         if not h:
             raise ValueError(err.value.decode())
         self._h = h
         self.n = L.orc_natoms(h)
+        if lattice is not None:
+            x = _Lattice()
+            for name, _ in _Lattice._fields_:
+                setattr(x, name, lattice[name])
+            if L.orc_set_lattice(h, C.byref(x), err, 256) != 0:
+                raise ValueError(err.value.decode())
         if ttm is not None:
             inst = sysd.get("instances")
-            over = inst[instance] if inst else {}
+            over = inst[index] if inst else {}
             t = _fill_ttm(ttm, over)
             if L.orc_set_ttm(h, C.byref(t), err, 256) != 0:
                 raise ValueError(err.value.decode())
@@ -342,3 +371,47 @@ class Oracle:
 
     def atom_cell(self, i):
         return lib().orc_atom_cell(self._h, int(i))
+
+    # -- moving lattice -------------------------------------------------------
+    def lattice_step(self, n):
+        lib().orc_lattice_step(self._h, int(n))
+
+    @property
+    def lattice_stepcount(self):
+        return lib().orc_lattice_stepcount(self._h)
+
+    def velocities(self):
+        out = np.empty((self.n, 3))
+        lib().orc_get_velocities(self._h, _dptr(out))
+        return out
+
+    def set_velocities(self, v):
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(self.n, 3)
+        lib().orc_set_velocities(self._h, _dptr(v))
+
+    def set_positions(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(self.n, 3)
+        lib().orc_set_positions(self._h, _dptr(x))
+
+    def forces(self):
+        out = np.empty((self.n, 3))
+        lib().orc_get_forces(self._h, _dptr(out))
+        return out
+
+    def lattice_energy(self):
+        k, m = C.c_double(), C.c_double()
+        lib().orc_lattice_energy(self._h, C.byref(k), C.byref(m))
+        return k.value, m.value
+
+    def total_energy(self):
+        k, m = self.lattice_energy()
+        o = self.observe()
+        return k + m + o[10] + o[11] + o[12]
+
+    @property
+    def colour_violations(self):
+        return lib().orc_colour_violations(self._h)
+
+    @property
+    def ion_energy_to_electrons(self):
+        return lib().orc_ion_energy_to_electrons(self._h)

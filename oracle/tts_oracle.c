@@ -196,6 +196,7 @@ struct orc_sys {
     orc_ttm t;
     int nc;                /* cells */
     double *Te, *Tl;
+    double *scratch;       /* 2 nc: per-sub-step increments */
     int *cell_of;          /* n */
     double cellvol;        /* m^3 */
     double dxc[3];         /* m */
@@ -206,9 +207,20 @@ struct orc_sys {
     /* samples */
     double *samples;
     int64_t nsamp, capsamp;
+    /* moving lattice */
+    int lattice_on;
+    orc_lattice L;
+    double mass;           /* kg */
+    double *vel;           /* 3n, m/s */
+    double *force;         /* 3n, N (Morse + magnetic) */
+    int *mor_start, *mor_j;/* Morse pair list, ascending j */
+    int64_t lstep;
+    int colour_violations;
+    double ion_to_e;       /* energy handed from ions to electrons, J */
 };
 
 static double sq(double x) { return x * x; }
+static void rebuild_lists(orc_sys *S);
 
 static const double BASIS_SC[1][3] = {{0, 0, 0}};
 static const double BASIS_BCC[2][3] = {{0, 0, 0}, {0.5, 0.5, 0.5}};
@@ -261,8 +273,10 @@ static int cmp_int(const void *a, const void *b)
 }
 
 /* Neighbour list: every j != i within the largest cutoff, by minimum image,
- * ascending j.  Lattices: scan cell offsets within the cutoff; cluster: all
- * pairs.  Pairs whose J is zero for their species are kept out. */
+ * ascending j.  Lattices: candidates from the cells within ceil(rc/a) of the
+ * atom's cell (a site in cell c + d is at least (|d_k| - 1) a away along axis
+ * k, so nothing closer than rc lies further out); clusters: all pairs.
+ * Pairs whose J is zero for their species are kept out. */
 static int build_neighbours(orc_sys *S, char *err, int errlen)
 {
     double rc = max_rc(&S->p);
@@ -273,13 +287,12 @@ static int build_neighbours(orc_sys *S, char *err, int errlen)
     S->nbr_j = malloc(sizeof(int) * totcap);
     S->nbr_J = malloc(sizeof(double) * totcap);
     int nb = S->p.lattice <= 2 ? basis_count(S->p.lattice) : 1;
-    int R = S->p.lattice <= 2 ? (int)ceil(rc / S->p.a) + 1 : 0;
+    int R = S->p.lattice <= 2 ? (int)ceil(rc / S->p.a) : 0;
     for (int i = 0; i < n; ++i) {
         int cnt = 0;
         if (S->p.lattice <= 2) {
-            int b = i % nb, cell = i / nb;
+            int cell = i / nb;
             int ix = cell % S->p.nx, iy = (cell / S->p.nx) % S->p.ny, iz = cell / (S->p.nx * S->p.ny);
-            (void)b;
             for (int dz = -R; dz <= R; ++dz)
                 for (int dy = -R; dy <= R; ++dy)
                     for (int dx = -R; dx <= R; ++dx)
@@ -289,6 +302,9 @@ static int build_neighbours(orc_sys *S, char *err, int errlen)
                             int jz = ((iz + dz) % S->p.nz + S->p.nz) % S->p.nz;
                             int j = ((jz * S->p.ny + jy) * S->p.nx + jx) * nb + b2;
                             if (j == i) continue;
+                            double d[3];
+                            min_image(S, i, j, d);
+                            if (sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) >= rc) continue;
                             if (cnt == cap) { cap *= 2; tmp = realloc(tmp, sizeof(int) * cap); }
                             tmp[cnt++] = j;
                         }
@@ -491,8 +507,9 @@ void orc_free(orc_sys *S)
     if (!S) return;
     free(S->pos); free(S->ipos2); free(S->species); free(S->colour);
     free(S->nbr_start); free(S->nbr_j); free(S->nbr_J); free(S->s);
-    free(S->Te); free(S->Tl); free(S->cell_of); free(S->src_shape);
+    free(S->Te); free(S->Tl); free(S->cell_of); free(S->src_shape); free(S->scratch);
     free(S->samples);
+    free(S->vel); free(S->force); free(S->mor_start); free(S->mor_j);
     free(S);
 }
 
@@ -514,14 +531,15 @@ static int cidx(const orc_sys *S, int cx, int cy, int cz)
 
 /* One TTM advance over Dt from time t_start, in S->substeps equal sub-steps,
  * on the given grids; returns the source energy deposited (J). */
-static double ttm_advance(const orc_sys *S, double *Te, double *Tl, double t_start, double Dt, double P0)
+/* use_G = 0 drops the G (T_e - T_l) exchange: with a moving lattice the ions
+ * exchange energy with the electrons through their own friction and noise. */
+static double ttm_advance(const orc_sys *S, double *Te, double *Tl, double t_start, double Dt, double P0, int use_G)
 {
     const orc_ttm *t = &S->t;
     int m = S->substeps;
     double dl = Dt / m;
     double sig = pulse_sigma(t), t0 = pulse_t0(t);
-    double *dE = malloc(sizeof(double) * S->nc);
-    double *dT = malloc(sizeof(double) * S->nc);
+    double *dE = S->scratch, *dT = S->scratch + S->nc;
     double dep = 0.0;
     int nd[3] = {t->ncx, t->ncy, t->ncz};
     for (int k = 0; k < m; ++k) {
@@ -542,8 +560,9 @@ static double ttm_advance(const orc_sys *S, double *Te, double *Tl, double t_sta
                         lap += (Tp - 2.0 * Te[c] + Tm) / (S->dxc[d] * S->dxc[d]);
                     }
                     double src = pulse * S->src_shape[c];
-                    dE[c] = dl * (t->kappa_e * lap - t->G * (Te[c] - Tl[c]) + src);
-                    dT[c] = dl * t->G * (Te[c] - Tl[c]) / t->C_l;
+                    double G = use_G ? t->G : 0.0;
+                    dE[c] = dl * (t->kappa_e * lap - G * (Te[c] - Tl[c]) + src);
+                    dT[c] = dl * G * (Te[c] - Tl[c]) / t->C_l;
                     dep += dl * src * S->cellvol;
                 }
         for (int c = 0; c < S->nc; ++c) {
@@ -552,8 +571,14 @@ static double ttm_advance(const orc_sys *S, double *Te, double *Tl, double t_sta
             Tl[c] += dT[c];
         }
     }
-    free(dE); free(dT);
     return dep;
+}
+
+/* Time step of the TTM grid: the spin step, or the lattice step when the
+ * lattice moves (the grid then advances once per lattice step). */
+static double ttm_dt(const orc_sys *S)
+{
+    return S->lattice_on ? S->L.spin_substeps * S->p.dt : S->p.dt;
 }
 
 /* Peak electron temperature over the step grid t_n of a TTM-only run. */
@@ -563,10 +588,11 @@ static double ttm_peak(const orc_sys *S, double P0)
     for (int c = 0; c < S->nc; ++c) { Te[c] = S->t.T0; Tl[c] = S->t.T0; }
     double sig = pulse_sigma(&S->t), t0 = pulse_t0(&S->t);
     double tend = t0 + 10.0 * sig;
-    int64_t nsteps = (int64_t)ceil(tend / S->p.dt);
+    double Dt = ttm_dt(S);
+    int64_t nsteps = (int64_t)ceil(tend / Dt);
     double peak = S->t.T0;
     for (int64_t n = 0; n < nsteps; ++n) {
-        ttm_advance(S, Te, Tl, n * S->p.dt, S->p.dt, P0);
+        ttm_advance(S, Te, Tl, n * Dt, Dt, P0, 1);
         for (int c = 0; c < S->nc; ++c) if (Te[c] > peak) peak = Te[c];
     }
     free(Te); free(Tl);
@@ -580,8 +606,9 @@ int orc_set_ttm(orc_sys *S, const orc_ttm *t, char *err, int errlen)
     S->t = *t;
     S->has_ttm = 1;
     S->nc = t->ncx * t->ncy * t->ncz;
-    free(S->Te); free(S->Tl); free(S->cell_of); free(S->src_shape);
+    free(S->Te); free(S->Tl); free(S->cell_of); free(S->src_shape); free(S->scratch);
     S->Te = malloc(sizeof(double) * S->nc);
+    S->scratch = malloc(sizeof(double) * 2 * S->nc);
     S->Tl = malloc(sizeof(double) * S->nc);
     S->src_shape = malloc(sizeof(double) * S->nc);
     S->cell_of = malloc(sizeof(int) * S->n);
@@ -617,7 +644,7 @@ int orc_set_ttm(orc_sys *S, const orc_ttm *t, char *err, int errlen)
     S->substeps = 1;
     if (d > 0 && t->kappa_e > 0.0) {
         double dmax = 0.4 * t->gamma_e * t->T0 * dxmin * dxmin / (t->kappa_e * d);
-        double m = ceil(S->p.dt / dmax);
+        double m = ceil(ttm_dt(S) / dmax);
         S->substeps = m < 1.0 ? 1 : (int)m;
     }
     S->P0 = t->P0;
@@ -636,6 +663,7 @@ int orc_set_ttm(orc_sys *S, const orc_ttm *t, char *err, int errlen)
         S->P0 = 0.5 * (lo + hi);
     }
     S->src_energy = 0.0;
+    if (S->lattice_on) rebuild_lists(S);   /* bath cells from the current positions */
     return 0;
 }
 
@@ -741,17 +769,23 @@ static void record_sample(orc_sys *S)
 /* One step t_n -> t_n+1: the bath reads T_e(t_n); passes p = 0..K-2 take
  * colours 0..K-2 with h = dt/2, pass K-1 takes colour K-1 with h = dt, passes
  * K..2K-2 take colours K-2..0 with h = dt/2; then the TTM grid advances. */
-void orc_step(orc_sys *S, int64_t nsteps)
+static void spin_sweep(orc_sys *S)
 {
     int K = S->ncolours;
     double dt = S->p.dt;
+    uint32_t pass = 0;
+    for (int c = 0; c < K - 1; ++c) colour_pass(S, c, 0.5 * dt, pass++);
+    colour_pass(S, K - 1, dt, pass++);
+    for (int c = K - 2; c >= 0; --c) colour_pass(S, c, 0.5 * dt, pass++);
+}
+
+void orc_step(orc_sys *S, int64_t nsteps)
+{
+    double dt = S->p.dt;
     for (int64_t it = 0; it < nsteps; ++it) {
-        uint32_t pass = 0;
-        for (int c = 0; c < K - 1; ++c) colour_pass(S, c, 0.5 * dt, pass++);
-        colour_pass(S, K - 1, dt, pass++);
-        for (int c = K - 2; c >= 0; --c) colour_pass(S, c, 0.5 * dt, pass++);
+        spin_sweep(S);
         if (S->has_ttm)
-            S->src_energy += ttm_advance(S, S->Te, S->Tl, S->step * dt, dt, S->P0);
+            S->src_energy += ttm_advance(S, S->Te, S->Tl, S->step * dt, dt, S->P0, 1);
         S->step++;
         if (S->p.sample_every > 0 && S->step % S->p.sample_every == 0) record_sample(S);
     }
@@ -810,6 +844,13 @@ void orc_observe(const orc_sys *S, double o[ORC_NOBS])
     } else {
         o[15] = S->p.T_bath; o[16] = S->p.T_bath;
     }
+    if (S->lattice_on) {
+        double ek, em;
+        orc_lattice_energy(S, &ek, &em);
+        o[16] = 2.0 * ek / (3.0 * S->n * KB);   /* ion kinetic temperature */
+        o[17] = ek;
+        o[18] = em;
+    }
     o[19] = (double)S->step;
 }
 
@@ -854,3 +895,329 @@ void orc_ttm_set(orc_sys *S, const double *Te, const double *Tl)
 }
 double orc_ttm_source_energy(const orc_sys *S) { return S->src_energy; }
 int orc_atom_cell(const orc_sys *S, int i) { return S->has_ttm ? S->cell_of[i] : 0; }
+
+/* ------------------------------------------------------------------------- */
+/* Moving lattice                                                            */
+/*                                                                           */
+/* One lattice step of length dtL = m dt (m = spin_substeps):                */
+/*   v += F dtL / 2M; m/2 spin steps; x += v dtL; new pair lists and J(r_ij);*/
+/*   m/2 spin steps; F = F_Morse + F_mag; v += F dtL / 2M;                   */
+/*   electron-ion coupling: v <- c1 v + c2 xi with c1 = exp(-gamma dtL / M), */
+/*   c2 = sqrt(k_B T_e (1 - c1^2) / M), the exact Ornstein-Uhlenbeck update  */
+/*   of the friction + noise force -gamma v + sqrt(2 gamma k_B T_e) xi(t),   */
+/*   whose kinetic-energy change is taken from the electrons of the atom's   */
+/*   TTM cell; then the TTM grid advances over dtL without its G term.       */
+/* F_mag,i = -sum_j J'(r_ij) (s_i.s_j) rhat_ij with rhat_ij from i to j, the  */
+/* exchange-mediated force of Sec. II.A; F_Morse,i = sum_j U'(r_ij) rhat_ij. */
+/* ------------------------------------------------------------------------- */
+/* Morse pair energy D [e^{-2a(r-r0)} - 2 e^{-a(r-r0)}] and its derivative */
+static double morse_raw(const orc_lattice *L, double r)
+{
+    double e1 = exp(-L->morse_alpha * (r - L->morse_r0));
+    return L->morse_D * (e1 * e1 - 2.0 * e1);
+}
+
+static double morse_raw_dU(const orc_lattice *L, double r)   /* J per angstrom */
+{
+    double e1 = exp(-L->morse_alpha * (r - L->morse_r0));
+    return 2.0 * L->morse_alpha * L->morse_D * (e1 - e1 * e1);
+}
+
+/* shifted-force form: energy and force both vanish at the cutoff,
+ * U_sf(r) = U(r) - U(rc) - (r - rc) U'(rc) */
+static double morse_U(const orc_lattice *L, double r)
+{
+    double rc = L->morse_rc;
+    return morse_raw(L, r) - morse_raw(L, rc) - (r - rc) * morse_raw_dU(L, rc);
+}
+
+static double morse_dU(const orc_lattice *L, double r)
+{
+    return morse_raw_dU(L, r) - morse_raw_dU(L, L->morse_rc);
+}
+
+static double pair_dJ(const orc_params *p, int ti, int tj, double r)   /* J per angstrom */
+{
+    const orc_exch *e = &p->exch[ti][tj];
+    if (e->kind != 2 || r >= e->rc) return 0.0;
+    return orc_bethe_slater_deriv(r, e->J1, e->J2, e->J3);
+}
+
+static void wrap_positions(orc_sys *S)
+{
+    for (int i = 0; i < S->n; ++i)
+        for (int k = 0; k < 3; ++k) {
+            double L = S->box[k];
+            double x = S->pos[3 * i + k];
+            x -= L * floor(x / L);
+            if (x >= L) x -= L;
+            S->pos[3 * i + k] = x;
+        }
+}
+
+/* all j != i with minimum-image distance below rc, ascending j, as CSR; cell
+ * list with cells no smaller than rc (brute force when fewer than 3 cells) */
+static void pairs_within(const orc_sys *S, double rc, int **pstart, int **pj)
+{
+    int n = S->n;
+    int nc[3], brute = 0;
+    for (int k = 0; k < 3; ++k) {
+        nc[k] = (int)floor(S->box[k] / rc);
+        if (nc[k] < 3) brute = 1;
+    }
+    int *start = malloc(sizeof(int) * (n + 1));
+    int cap = n * 16 + 16, total = 0;
+    int *jl = malloc(sizeof(int) * cap);
+    int *head = NULL, *next = NULL, *cellof = NULL;
+    if (!brute) {
+        head = malloc(sizeof(int) * nc[0] * nc[1] * nc[2]);
+        next = malloc(sizeof(int) * n);
+        cellof = malloc(sizeof(int) * n * 3);
+        for (int c = 0; c < nc[0] * nc[1] * nc[2]; ++c) head[c] = -1;
+        for (int i = n - 1; i >= 0; --i) {
+            int cc[3];
+            for (int k = 0; k < 3; ++k) {
+                cc[k] = (int)floor(S->pos[3 * i + k] / S->box[k] * nc[k]);
+                if (cc[k] >= nc[k]) cc[k] = nc[k] - 1;
+                if (cc[k] < 0) cc[k] = 0;
+                cellof[3 * i + k] = cc[k];
+            }
+            int c = (cc[2] * nc[1] + cc[1]) * nc[0] + cc[0];
+            next[i] = head[c];
+            head[c] = i;
+        }
+    }
+    int tcap = 64, *tmp = malloc(sizeof(int) * tcap);
+    for (int i = 0; i < n; ++i) {
+        int cnt = 0;
+        if (brute) {
+            for (int j = 0; j < n; ++j) {
+                if (j == i) continue;
+                double d[3];
+                min_image(S, i, j, d);
+                if (sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) >= rc) continue;
+                if (cnt == tcap) { tcap *= 2; tmp = realloc(tmp, sizeof(int) * tcap); }
+                tmp[cnt++] = j;
+            }
+        } else {
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int cx = (cellof[3 * i] + dx + nc[0]) % nc[0];
+                        int cy = (cellof[3 * i + 1] + dy + nc[1]) % nc[1];
+                        int cz = (cellof[3 * i + 2] + dz + nc[2]) % nc[2];
+                        for (int j = head[(cz * nc[1] + cy) * nc[0] + cx]; j >= 0; j = next[j]) {
+                            if (j == i) continue;
+                            double d[3];
+                            min_image(S, i, j, d);
+                            if (sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) >= rc) continue;
+                            if (cnt == tcap) { tcap *= 2; tmp = realloc(tmp, sizeof(int) * tcap); }
+                            tmp[cnt++] = j;
+                        }
+                    }
+        }
+        qsort(tmp, cnt, sizeof(int), cmp_int);
+        start[i] = total;
+        for (int k = 0; k < cnt; ++k) {
+            if (total == cap) { cap *= 2; jl = realloc(jl, sizeof(int) * cap); }
+            jl[total++] = tmp[k];
+        }
+    }
+    start[n] = total;
+    free(tmp); free(head); free(next); free(cellof);
+    *pstart = start;
+    *pj = jl;
+}
+
+/* exchange list with J(r) at the current positions, Morse list, colour check */
+static void rebuild_lists(orc_sys *S)
+{
+    int *st, *jj;
+    pairs_within(S, max_rc(&S->p), &st, &jj);
+    free(S->nbr_start); free(S->nbr_j); free(S->nbr_J);
+    S->nbr_start = malloc(sizeof(int) * (S->n + 1));
+    S->nbr_j = malloc(sizeof(int) * (st[S->n] + 1));
+    S->nbr_J = malloc(sizeof(double) * (st[S->n] + 1));
+    int total = 0;
+    S->colour_violations = 0;
+    for (int i = 0; i < S->n; ++i) {
+        S->nbr_start[i] = total;
+        for (int k = st[i]; k < st[i + 1]; ++k) {
+            int j = jj[k];
+            double d[3];
+            min_image(S, i, j, d);
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double J = pair_J(&S->p, S->species[i], S->species[j], r);
+            if (J == 0.0) continue;
+            if (S->colour[i] == S->colour[j]) S->colour_violations++;
+            S->nbr_j[total] = j;
+            S->nbr_J[total] = J;
+            ++total;
+        }
+    }
+    S->nbr_start[S->n] = total;
+    free(st); free(jj);
+    free(S->mor_start); free(S->mor_j);
+    pairs_within(S, S->L.morse_rc, &S->mor_start, &S->mor_j);
+    /* bath cell of each atom from its current position */
+    if (S->has_ttm) {
+        int nd[3] = {S->t.ncx, S->t.ncy, S->t.ncz};
+        for (int i = 0; i < S->n; ++i) {
+            int cc[3];
+            for (int d = 0; d < 3; ++d) {
+                double f = S->pos[3 * i + d] / S->box[d];
+                cc[d] = (int)floor(f * nd[d]);
+                if (cc[d] >= nd[d]) cc[d] = nd[d] - 1;
+                if (cc[d] < 0) cc[d] = 0;
+            }
+            S->cell_of[i] = (cc[2] * nd[1] + cc[1]) * nd[0] + cc[0];
+        }
+    }
+}
+
+static void compute_forces(orc_sys *S)
+{
+    for (int k = 0; k < 3 * S->n; ++k) S->force[k] = 0.0;
+    for (int i = 0; i < S->n; ++i) {
+        for (int k = S->mor_start[i]; k < S->mor_start[i + 1]; ++k) {
+            int j = S->mor_j[k];
+            double d[3];
+            min_image(S, i, j, d);
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double f = morse_dU(&S->L, r) * 1e10;          /* N */
+            for (int c = 0; c < 3; ++c) S->force[3 * i + c] += f * d[c] / r;
+        }
+        for (int k = S->nbr_start[i]; k < S->nbr_start[i + 1]; ++k) {
+            int j = S->nbr_j[k];
+            double d[3];
+            min_image(S, i, j, d);
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            const double *si = &S->s[3 * i], *sj = &S->s[3 * j];
+            double ss = si[0] * sj[0] + si[1] * sj[1] + si[2] * sj[2];
+            double f = -pair_dJ(&S->p, S->species[i], S->species[j], r) * ss * 1e10;
+            for (int c = 0; c < 3; ++c) S->force[3 * i + c] += f * d[c] / r;
+        }
+    }
+}
+
+int orc_set_lattice(orc_sys *S, const orc_lattice *L, char *err, int errlen)
+{
+    if (!S->periodic) { snprintf(err, errlen, "a moving lattice needs a periodic lattice"); return -1; }
+    if (S->has_ttm) { snprintf(err, errlen, "set the moving lattice before the TTM grid"); return -1; }
+    if (L->spin_substeps < 2 || L->spin_substeps % 2) { snprintf(err, errlen, "spin_substeps must be even"); return -1; }
+    if (!(L->mass_amu > 0.0) || !(L->morse_rc > 0.0)) { snprintf(err, errlen, "bad lattice parameters"); return -1; }
+    for (int k = 0; k < 3; ++k)
+        if (S->box[k] <= 2.0 * L->morse_rc) { snprintf(err, errlen, "box must exceed twice the pair cutoff"); return -1; }
+    S->L = *L;
+    S->lattice_on = 1;
+    S->mass = L->mass_amu * 1.66053906660e-27;
+    S->vel = realloc(S->vel, sizeof(double) * 3 * S->n);
+    S->force = realloc(S->force, sizeof(double) * 3 * S->n);
+    /* initial longitudinal strain wave along z, one wavelength per box */
+    double Lz = S->box[2];
+    for (int i = 0; i < S->n; ++i) {
+        double z0 = S->pos[3 * i + 2];
+        S->pos[3 * i + 2] = z0 + L->strain_amp * Lz / (2.0 * PI) * sin(2.0 * PI * z0 / Lz);
+    }
+    wrap_positions(S);
+    /* Maxwell-Boltzmann velocities (Philox counter (atom, 0, 0xFFFF0003, instance)),
+     * net momentum removed */
+    uint32_t key[2] = {(uint32_t)(S->p.seed & 0xffffffffu), (uint32_t)(S->p.seed >> 32)};
+    double vs = sqrt(KB * L->T_init / S->mass), mean[3] = {0, 0, 0};
+    for (int i = 0; i < S->n; ++i) {
+        uint32_t ctr[4] = {(uint32_t)i, 0u, 0xFFFF0003u, S->p.instance}, w[4];
+        double g[3];
+        orc_philox4x32_10(ctr, key, w);
+        orc_gauss3(w, g);
+        for (int k = 0; k < 3; ++k) { S->vel[3 * i + k] = vs * g[k]; mean[k] += S->vel[3 * i + k]; }
+    }
+    for (int i = 0; i < S->n; ++i)
+        for (int k = 0; k < 3; ++k) S->vel[3 * i + k] -= mean[k] / S->n;
+    S->lstep = 0;
+    S->ion_to_e = 0.0;
+    rebuild_lists(S);
+    compute_forces(S);
+    return 0;
+}
+
+void orc_lattice_step(orc_sys *S, int64_t nsteps)
+{
+    int m = S->L.spin_substeps;
+    double dtL = m * S->p.dt;
+    double M = S->mass;
+    uint32_t key[2] = {(uint32_t)(S->p.seed & 0xffffffffu), (uint32_t)(S->p.seed >> 32)};
+    double *dEc = S->has_ttm ? calloc(S->nc, sizeof(double)) : NULL;
+    for (int64_t it = 0; it < nsteps; ++it) {
+        for (int k = 0; k < 3 * S->n; ++k) S->vel[k] += S->force[k] * dtL / (2.0 * M);
+        for (int k = 0; k < m / 2; ++k) { spin_sweep(S); S->step++; }
+        for (int k = 0; k < 3 * S->n; ++k) S->pos[k] += S->vel[k] * dtL * 1e10;
+        wrap_positions(S);
+        rebuild_lists(S);
+        for (int k = 0; k < m / 2; ++k) { spin_sweep(S); S->step++; }
+        compute_forces(S);
+        for (int k = 0; k < 3 * S->n; ++k) S->vel[k] += S->force[k] * dtL / (2.0 * M);
+        if (S->L.gamma_p > 0.0) {
+            double c1 = exp(-S->L.gamma_p * dtL / M);
+            if (dEc) for (int c = 0; c < S->nc; ++c) dEc[c] = 0.0;
+            for (int i = 0; i < S->n; ++i) {
+                double T = bath_T(S, i);
+                double c2 = sqrt(KB * T * (1.0 - c1 * c1) / M);
+                uint32_t ctr[4] = {(uint32_t)i, (uint32_t)S->lstep, 0xFFFF0002u, S->p.instance}, w[4];
+                double g[3], ke0 = 0.0, ke1 = 0.0;
+                orc_philox4x32_10(ctr, key, w);
+                orc_gauss3(w, g);
+                for (int k = 0; k < 3; ++k) {
+                    double v0 = S->vel[3 * i + k];
+                    double v1 = c1 * v0 + c2 * g[k];
+                    ke0 += 0.5 * M * v0 * v0;
+                    ke1 += 0.5 * M * v1 * v1;
+                    S->vel[3 * i + k] = v1;
+                }
+                S->ion_to_e -= ke1 - ke0;
+                if (dEc) dEc[S->cell_of[i]] -= ke1 - ke0;
+            }
+            if (dEc)
+                for (int c = 0; c < S->nc; ++c) {
+                    double Ee = 0.5 * S->t.gamma_e * S->Te[c] * S->Te[c] + dEc[c] / S->cellvol;
+                    S->Te[c] = sqrt(2.0 * Ee / S->t.gamma_e);
+                }
+        }
+        if (S->has_ttm)
+            S->src_energy += ttm_advance(S, S->Te, S->Tl, S->lstep * dtL, dtL, S->P0, 0);
+        S->lstep++;
+        if (S->p.sample_every > 0 && S->lstep % S->p.sample_every == 0) record_sample(S);
+    }
+    free(dEc);
+}
+
+int64_t orc_lattice_stepcount(const orc_sys *S) { return S->lstep; }
+void orc_get_velocities(const orc_sys *S, double *out) { memcpy(out, S->vel, sizeof(double) * 3 * S->n); }
+void orc_set_velocities(orc_sys *S, const double *in) { memcpy(S->vel, in, sizeof(double) * 3 * S->n); }
+void orc_set_positions(orc_sys *S, const double *in)
+{
+    memcpy(S->pos, in, sizeof(double) * 3 * S->n);
+    wrap_positions(S);
+    if (S->lattice_on) {
+        rebuild_lists(S);
+        compute_forces(S);
+    }
+}
+void orc_get_forces(const orc_sys *S, double *out) { memcpy(out, S->force, sizeof(double) * 3 * S->n); }
+void orc_lattice_energy(const orc_sys *S, double *kin, double *morse)
+{
+    double ek = 0.0, em = 0.0;
+    for (int i = 0; i < S->n; ++i) {
+        for (int k = 0; k < 3; ++k) ek += 0.5 * S->mass * S->vel[3 * i + k] * S->vel[3 * i + k];
+        for (int k = S->mor_start[i]; k < S->mor_start[i + 1]; ++k) {
+            int j = S->mor_j[k];
+            if (j <= i) continue;
+            double d[3];
+            min_image(S, i, j, d);
+            em += morse_U(&S->L, sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+        }
+    }
+    *kin = ek;
+    *morse = em;
+}
+int orc_colour_violations(const orc_sys *S) { return S->colour_violations; }
+double orc_ion_energy_to_electrons(const orc_sys *S) { return S->ion_to_e; }

@@ -65,6 +65,20 @@ typedef struct {
     double depth_z;         /* angstrom */
 } orc_ttm;
 
+/* Moving lattice (paper Sec. II.A: positions under the pair potential plus the
+ * exchange-mediated force -dJ/dr (s_i.s_j), advanced together with the spins). */
+typedef struct {
+    double mass_amu;      /* atomic mass */
+    double morse_D;       /* J */
+    double morse_alpha;   /* 1/angstrom */
+    double morse_r0;      /* angstrom */
+    double morse_rc;      /* angstrom; the energy is shifted to zero there */
+    int spin_substeps;    /* spin steps per lattice step (even, >= 2) */
+    double strain_amp;    /* initial u_z = A Lz / (2 pi) sin(2 pi z / Lz) */
+    double T_init;        /* initial ion temperature, K */
+    double gamma_p;       /* electron-ion friction coefficient, kg/s (0: none) */
+} orc_lattice;
+
 typedef struct orc_sys orc_sys;
 
 /* Philox4x32-10 block function (Salmon et al., SC'11). */
@@ -111,5 +125,17 @@ void orc_ttm_get(const orc_sys *s, double *Te, double *Tl);
 void orc_ttm_set(orc_sys *s, const double *Te, const double *Tl);
 double orc_ttm_source_energy(const orc_sys *s);
 int orc_atom_cell(const orc_sys *s, int i);
+
+int orc_set_lattice(orc_sys *s, const orc_lattice *L, char *err, int errlen);
+void orc_lattice_step(orc_sys *s, int64_t nsteps);
+int64_t orc_lattice_stepcount(const orc_sys *s);
+void orc_get_velocities(const orc_sys *s, double *out);   /* m/s */
+void orc_set_positions(orc_sys *s, const double *in);     /* angstrom; rebuilds lists and forces */
+void orc_set_velocities(orc_sys *s, const double *in);
+void orc_get_forces(const orc_sys *s, double *out);       /* N, Morse + magnetic */
+/* kinetic and pair-potential energies (J) */
+void orc_lattice_energy(const orc_sys *s, double *kinetic, double *morse);
+int orc_colour_violations(const orc_sys *s);
+double orc_ion_energy_to_electrons(const orc_sys *s);
 
 #endif

@@ -66,6 +66,14 @@ class tts_ttm_desc(C.Structure):
     ]
 
 
+class tts_lattice_desc(C.Structure):
+    _fields_ = [
+        ("mass_amu", C.c_double), ("morse_D", C.c_double), ("morse_alpha", C.c_double),
+        ("morse_r0", C.c_double), ("morse_rc", C.c_double), ("spin_substeps", C.c_int),
+        ("strain_amp", C.c_double), ("T_init", C.c_double), ("gamma_p", C.c_double), ("skin", C.c_double),
+    ]
+
+
 class tts_info_t(C.Structure):
     _fields_ = [("n_total", C.c_int64), ("n_instances", C.c_int), ("engine", C.c_int),
                 ("precision", C.c_int), ("max_colours", C.c_int), ("steps_done", C.c_int64),
@@ -98,6 +106,9 @@ _SIG = {
     "tts_info": [C.c_void_p, _P(tts_info_t)],
     "tts_profile_enable": [C.c_void_p, C.c_int],
     "tts_profile_read": [C.c_void_p, _P(C.c_double), _P(C.c_int64), _P(C.c_int64)],
+    "tts_set_lattice": [C.c_void_p, _P(tts_lattice_desc)],
+    "tts_get_positions": [C.c_void_p, C.c_int, _P(C.c_double)],
+    "tts_get_velocities": [C.c_void_p, C.c_int, _P(C.c_double)],
     "tts_ttm_advance_noalloc": [_P(tts_ttm_desc), _P(C.c_double), C.c_double, C.c_int64, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p],
 }
@@ -225,8 +236,10 @@ class System:
     """A system of one or more instances on the GPU (tts_create_system)."""
 
     def __init__(self, sysd, ttm=None, precision=64, engine="auto", stream=None, obs_capacity=0,
-                 instance_base=0):
+                 instance_base=0, lattice=None):
         L = load()
+        if lattice is not None and engine == "auto":
+            engine = "general"
         d, keep = make_desc(sysd, precision, engine, obs_capacity, instance_base)
         h = C.c_void_p()
         _check(L.tts_create_system(C.byref(d), C.c_void_p(stream or 0), C.byref(h)))
@@ -242,6 +255,8 @@ class System:
             k = C.c_int()
             _check(L.tts_instance_size(self._h, i, C.byref(n), C.byref(k)))
             self.sizes.append((n.value, k.value))
+        if lattice is not None:
+            self.set_lattice(lattice)
         if ttm is not None:
             self.set_ttm_grid(ttm)
 
@@ -342,6 +357,29 @@ class System:
         _check(load().tts_info(self._h, C.byref(i)))
         return i
 
+    def set_lattice(self, lat):
+        x = tts_lattice_desc()
+        for name, _ in tts_lattice_desc._fields_:
+            if name == "skin":
+                x.skin = float(lat.get("skin", 1.0))
+            else:
+                setattr(x, name, lat[name])
+        _check(load().tts_set_lattice(self._h, C.byref(x)))
+
+    def get_positions(self, inst=0):
+        out = np.empty((self.sizes[inst][0], 3))
+        _check(load().tts_get_positions(self._h, int(inst), _dp(out)))
+        return out
+
+    def get_velocities(self, inst=0):
+        out = np.empty((self.sizes[inst][0], 3))
+        _check(load().tts_get_velocities(self._h, int(inst), _dp(out)))
+        return out
+
+    def engine_now(self):
+        """Engine in use now (it can change when a TTM grid is attached)."""
+        return ENGINE_NAME.get(self.info().engine, self.info().engine)
+
     def profile_enable(self, on=True):
         _check(load().tts_profile_enable(self._h, 1 if on else 0))
 
@@ -365,6 +403,6 @@ def ttm_advance_noalloc(ttm, box_ang, dt, step, dev_Te, dev_Tl, dev_deposited=0,
 
 
 def create_system(sysd, ttm=None, precision=64, engine="auto", stream=None, obs_capacity=0,
-                  instance_base=0):
-    """tts_create_system (+ tts_set_ttm_grid when ttm is given)."""
-    return System(sysd, ttm, precision, engine, stream, obs_capacity, instance_base)
+                  instance_base=0, lattice=None):
+    """tts_create_system (+ tts_set_lattice, tts_set_ttm_grid when given)."""
+    return System(sysd, ttm, precision, engine, stream, obs_capacity, instance_base, lattice)

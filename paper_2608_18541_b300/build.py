@@ -13,7 +13,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libtts.so")
 OBJDIR = os.path.join(HERE, "_build")
 
-SOURCES = ["tts_build.cpp", "tts_kernels.cu", "tts_engines.cu", "tts_runtime.cu", "tts_noalloc.cu"]
+SOURCES = ["tts_build.cpp", "tts_kernels.cu", "tts_engines.cu", "tts_runtime.cu", "tts_noalloc.cu", "tts_lattice.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

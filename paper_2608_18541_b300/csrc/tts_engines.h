@@ -33,10 +33,12 @@ const char *engine_last_error();
 cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuffers &b, const TtmParams &tp,
                                bool ttm_active, cudaStream_t st, int *kernels, cudaEvent_t ev_begin,
                                cudaEvent_t ev_end);
-// Spins of one instance in general slot order (relative to the instance).
-int engine_read_spins(EngineState *e, int inst, void *x, void *y, void *z, cudaStream_t st);
-int engine_write_spins(EngineState *e, int inst, const void *x, const void *y, const void *z, cudaStream_t st);
-// A TTM grid was attached: new cell map in general slot order.
+// Engines that advance many steps in one launch (resident): run nsteps steps.
+bool engine_multi_step(const EngineState *e);
+cudaError_t engine_run_steps(EngineState *e, const StepParams &p, const DevBuffers &b, const TtmParams &tp,
+                             bool ttm_active, int64_t nsteps, cudaStream_t st, int *kernels, cudaEvent_t ev_begin,
+                             cudaEvent_t ev_end);
+// A TTM grid was attached (the cell map of every slot is in DevBuffers::cell).
 int engine_set_cells(EngineState *e, const std::vector<DevInstance> &dinst, const std::vector<int> &cellmap,
                      cudaStream_t st);
 cudaError_t engine_sync_to_general(EngineState *e, const DevBuffers &b, cudaStream_t st);

@@ -269,7 +269,8 @@ template <typename R>
 __global__ void __launch_bounds__(kObsBlock) obs_partial_kernel(StepParams p, DevBuffers b, int mode)
 {
     const int64_t step = *b.step;
-    if (mode == 0 && (p.sample_every <= 0 || (step + 1) % p.sample_every != 0)) return;
+    const int64_t clock = p.lattice_on ? *p.lstep : step;
+    if (mode == 0 && (p.sample_every <= 0 || (clock + 1) % p.sample_every != 0)) return;
     const int inst = b.obs_block_inst[blockIdx.x];
     const DevInstance I = b.inst[inst];
     const int64_t first = b.obs_block_begin[blockIdx.x];
@@ -330,7 +331,8 @@ __global__ void __launch_bounds__(kObsBlock) obs_partial_kernel(StepParams p, De
 __global__ void obs_final_kernel(StepParams p, DevBuffers b, int mode)
 {
     const int64_t step = *b.step;
-    const bool sample = (mode == 1) || (p.sample_every > 0 && (step + 1) % p.sample_every == 0);
+    const int64_t clock = p.lattice_on ? *p.lstep : step;
+    const bool sample = (mode == 1) || (p.sample_every > 0 && (clock + 1) % p.sample_every == 0);
     if (sample) {
         for (int inst = threadIdx.x; inst < p.n_instances; inst += blockDim.x) {
             const DevInstance I = b.inst[inst];
@@ -340,7 +342,8 @@ __global__ void obs_final_kernel(StepParams p, DevBuffers b, int mode)
                 for (int k = 0; k < kObsFields; ++k) tot[k] += b.obs_partial[int64_t(blk) * kObsFields + k];
             double rec[TTS_NOBS];
             for (int k = 0; k < TTS_NOBS; ++k) rec[k] = 0.0;
-            const int64_t sstep = mode == 0 ? step + 1 : step;
+            // a moving lattice has advanced the spin-step counter already
+            const int64_t sstep = (mode == 0 && !p.lattice_on) ? step + 1 : step;
             rec[0] = double(sstep) * p.dt;
             double musum = 0.0, mux = 0.0, muy = 0.0, muz = 0.0;
             for (int t = 0; t < TTS_MAX_SPECIES; ++t) {
@@ -371,6 +374,16 @@ __global__ void obs_final_kernel(StepParams p, DevBuffers b, int mode)
             }
             rec[15] = te / I.ncells;
             rec[16] = tl / I.ncells;
+            if (p.lattice_on && mode == 0) {
+                double ek = 0.0, em = 0.0;
+                for (int blk = I.obs_block_begin; blk < I.obs_block_begin + I.obs_block_count; ++blk) {
+                    ek += p.lat_partial[2 * int64_t(blk)];
+                    em += p.lat_partial[2 * int64_t(blk) + 1];
+                }
+                rec[16] = 2.0 * ek / (3.0 * double(I.n) * kBoltzmann);
+                rec[17] = ek;
+                rec[18] = em;
+            }
             rec[19] = double(sstep);
             double *dst;
             if (mode == 0) {
@@ -384,10 +397,88 @@ __global__ void obs_final_kernel(StepParams p, DevBuffers b, int mode)
         }
     }
     __syncthreads();
-    if (mode == 0 && threadIdx.x == 0) *b.step = step + 1;
+    if (mode == 0 && !p.lattice_on && threadIdx.x == 0) *b.step = step + 1;
+}
+
+// ---------------------------------------------------------------------------
+// Source calibration, one block per job.  The TTM-only run uses the same
+// update as ttm_kernel; every thread keeps the running maximum of its cells
+// and the block reduces it once per run.
+// ---------------------------------------------------------------------------
+__device__ double calib_peak(CalibJob &J, double P0, double dt, const TtmParams &tp, double *red)
+{
+    const int nx = J.cells[0], ny = J.cells[1], nz = J.cells[2], nc = nx * ny * nz;
+    double *Te = J.work, *Tl = J.work + nc, *dE = J.work + 2 * nc;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        Te[c] = tp.T0;
+        Tl[c] = tp.T0;
+    }
+    __syncthreads();
+    const double delta = dt / J.substeps;
+    double peak = tp.T0;
+    for (int64_t n = 0; n < J.nsteps; ++n) {
+        for (int k = 0; k < J.substeps; ++k) {
+            const double tt = double(n) * dt + double(k) * delta;
+            const double z = (tt - J.t0) / J.sigma_t;
+            const double pulse = P0 * exp(-0.5 * z * z);
+            for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+                const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+                const double Tc = Te[c];
+                double lap = 0.0;
+                if (nx > 1)
+                    lap += (Te[(cz * ny + cy) * nx + (cx + 1) % nx] - 2.0 * Tc + Te[(cz * ny + cy) * nx + (cx + nx - 1) % nx]) /
+                           (J.dx[0] * J.dx[0]);
+                if (ny > 1)
+                    lap += (Te[(cz * ny + (cy + 1) % ny) * nx + cx] - 2.0 * Tc + Te[(cz * ny + (cy + ny - 1) % ny) * nx + cx]) /
+                           (J.dx[1] * J.dx[1]);
+                if (nz > 1)
+                    lap += (Te[(((cz + 1) % nz) * ny + cy) * nx + cx] - 2.0 * Tc +
+                            Te[(((cz + nz - 1) % nz) * ny + cy) * nx + cx]) / (J.dx[2] * J.dx[2]);
+                const double x = tp.G * (Tc - Tl[c]);
+                dE[c] = delta * (tp.kappa_e * lap - x + pulse * J.shape[c]);
+                Tl[c] += delta * x / tp.C_l;
+            }
+            __syncthreads();
+            for (int c = threadIdx.x; c < nc; c += blockDim.x)
+                Te[c] = sqrt(2.0 * (0.5 * tp.gamma_e * Te[c] * Te[c] + dE[c]) / tp.gamma_e);
+            __syncthreads();
+        }
+        for (int c = threadIdx.x; c < nc; c += blockDim.x) peak = fmax(peak, Te[c]);
+    }
+    red[threadIdx.x] = peak;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void calibrate_kernel(CalibJob *jobs, double dt, TtmParams tp)
+{
+    __shared__ double red[256];
+    CalibJob &J = jobs[blockIdx.x];
+    double hi = J.guess;
+    // at most 200 doublings: the peak grows without bound with P0
+    for (int it = 0; it < 200 && calib_peak(J, hi, dt, tp, red) < J.target; ++it) hi *= 2.0;
+    double lo = 0.0;
+    for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (calib_peak(J, mid, dt, tp, red) < J.target) lo = mid; else hi = mid;
+    }
+    if (threadIdx.x == 0) J.P0 = 0.5 * (lo + hi);
 }
 
 }  // namespace
+
+cudaError_t launch_calibrate(CalibJob *jobs_dev, int njobs, int ncells, double dt, const TtmParams &tp, cudaStream_t st)
+{
+    if (njobs <= 0) return cudaSuccess;
+    calibrate_kernel<<<njobs, ncells <= 32 ? 32 : 256, 0, st>>>(jobs_dev, dt, tp);
+    return cudaGetLastError();
+}
 
 // ---------------------------------------------------------------------------
 cudaError_t launch_sigma(const StepParams &p, const DevBuffers &b, int ncells, int precision, cudaStream_t st)

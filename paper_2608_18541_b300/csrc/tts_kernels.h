@@ -20,6 +20,11 @@ struct StepParams {
     int instance_base;       // global id of instance 0 (Philox counter word 3)
     int sample_every;
     int obs_capacity;
+    int ncells_total;        // TTM cells over all instances (host-side launch size)
+    int obs_blocks;          // observable partial blocks (host-side launch size)
+    int lattice_on;          // observables of a moving lattice (sampled per lattice step)
+    int64_t *lstep;          // lattice step counter (moving lattice)
+    double *lat_partial;     // per observable block: kinetic and pair energy (moving lattice)
 };
 
 // Device buffers of a system (general engine layout, real_t = float or double).
@@ -53,6 +58,9 @@ constexpr int kObsBlock = 128;       // threads of an observable block
 enum HealthBits : unsigned int {
     kHealthNonFinite = 1u,
     kHealthTimeout = 2u,
+    kHealthSkin = 4u,        // an atom left its neighbour-list skin
+    kHealthColour = 8u,      // two exchange-coupled atoms share a colour
+    kHealthOverflow = 16u,   // more exchange neighbours than the table holds
 };
 
 cudaError_t launch_sigma(const StepParams &p, const DevBuffers &b, int ncells_total, int precision,
@@ -63,5 +71,23 @@ cudaError_t launch_ttm(const StepParams &p, const DevBuffers &b, const TtmParams
                        cudaStream_t st);
 cudaError_t launch_obs(const StepParams &p, const DevBuffers &b, int precision, int nblocks, int mode,
                        cudaStream_t st);
+
+// One source-power calibration: find P0 such that the largest T_e over the
+// cells and the step times t_n of a TTM-only run (to t0 + 10 sigma_t) equals
+// `target`, by 60 bisection steps after doubling an initial upper bound.
+struct CalibJob {
+    int cells[3];
+    int substeps;
+    double dx[3];
+    double sigma_t, t0;
+    double target;
+    double guess;              // initial upper bound
+    int64_t nsteps;            // step times to scan
+    const double *shape;       // per cell source profile (device)
+    double *work;              // 3 * ncells doubles of device scratch
+    double P0;                 // result
+};
+
+cudaError_t launch_calibrate(CalibJob *jobs_dev, int njobs, int ncells, double dt, const TtmParams &tp, cudaStream_t st);
 
 }  // namespace tts

@@ -23,14 +23,38 @@ struct u32x4 {
 
 TTS_HD void mul_hi_lo(uint32_t a, uint32_t b, uint32_t &hi, uint32_t &lo)
 {
-#ifdef __CUDA_ARCH__
-    lo = a * b;
-    hi = __umulhi(a, b);
-#else
-    uint64_t p = static_cast<uint64_t>(a) * static_cast<uint64_t>(b);
+    // one widening multiply gives both halves
+    const uint64_t p = static_cast<uint64_t>(a) * static_cast<uint64_t>(b);
     hi = static_cast<uint32_t>(p >> 32);
     lo = static_cast<uint32_t>(p);
+}
+
+// Division of n < 2^31 by an invariant d >= 1 with one multiply-high, add and
+// shift (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// q = (mulhi(m, n) + n) >> l.
+struct FastDiv {
+    uint32_t d, m, l;
+};
+
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    FastDiv f;
+    f.d = d;
+    f.l = 0;
+    while ((1ull << f.l) < d) ++f.l;
+    f.m = static_cast<uint32_t>(((1ull << 32) * ((1ull << f.l) - d)) / d + 1);
+    return f;
+}
+
+TTS_HD uint32_t fast_div(uint32_t n, const FastDiv &f)
+{
+#ifdef __CUDA_ARCH__
+    const uint32_t t = __umulhi(f.m, n);
+#else
+    const uint32_t t = static_cast<uint32_t>((static_cast<uint64_t>(f.m) * n) >> 32);
 #endif
+    return (t + n) >> f.l;
 }
 
 TTS_HD u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1)

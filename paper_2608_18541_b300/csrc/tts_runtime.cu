@@ -13,72 +13,37 @@
 #include "tts_engines.h"
 #include "tts_internal.h"
 #include "tts_kernels.h"
+#include "tts_system.h"
 
 using namespace tts;
 
 namespace {
-
 thread_local std::string g_error = "no error";
+}  // namespace
 
-int fail(int code, const std::string &msg)
+void tts::set_last_error(const std::string &msg) { g_error = msg; }
+
+int tts::fail(int code, const std::string &msg)
 {
     g_error = msg;
     return code;
 }
 
-int cuda_fail(cudaError_t e, const char *what)
+int tts::cuda_fail(cudaError_t e, const char *what)
 {
     g_error = std::string(what) + ": " + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? TTS_ERR_OOM : TTS_ERR_CUDA;
 }
 
-#define TTS_CUDA(call, what)                          \
-    do {                                              \
-        cudaError_t e_ = (call);                      \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-    } while (0)
+int tts::upload(void *dst, const void *src, size_t bytes, cudaStream_t st, const char *what)
+{
+    if (bytes == 0) return TTS_OK;
+    TTS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), what);
+    TTS_CUDA(cudaStreamSynchronize(st), what);
+    return TTS_OK;
+}
 
-}  // namespace
 
-void tts::set_last_error(const std::string &msg) { g_error = msg; }
-
-struct tts_system {
-    tts_system_desc desc{};
-    int precision = 32;
-    size_t rsize = 4;
-    int engine = TTS_ENGINE_GENERAL;
-    cudaStream_t stream = nullptr;     // caller's stream
-    cudaStream_t capture = nullptr;    // private stream used only to capture graphs
-    int64_t n_total = 0;
-    int n_inst = 0;
-    int zmax = 0;
-    int max_colours = 1;
-    int max_passes = 1;
-    std::vector<HostInstance> host;                 // built instances (canonical order)
-    std::vector<std::vector<int64_t>> slot_of_atom; // per instance: atom -> slot (relative)
-    std::vector<DevInstance> dinst;
-    std::vector<PassRange> ranges;
-    std::vector<int64_t> pass_offset;               // ranges of pass p: [off[p], off[p+1])
-    std::vector<int64_t> pass_work;
-    int ncells_total = 0;
-    bool ttm_active = false;
-    TtmParams tp{};
-    std::vector<double> P0;                         // per instance
-    std::vector<double> inst_peak, inst_fwhm;       // per-instance pulse overrides (may be empty)
-    int obs_blocks = 0;
-    int obs_capacity = 1024;
-    DevBuffers b;
-    StepParams p{};
-    cudaGraphExec_t graph = nullptr;
-    int kernels_per_step = 0;
-    int64_t launches = 0;
-    bool dirty = true;
-    EngineState *eng = nullptr;                     // fast-engine state, if any
-    bool profiling = false;
-    std::vector<cudaEvent_t> prof_events;           // begin/end pairs of profiled steps
-    double prof_ms = 0.0;
-    int64_t prof_steps = 0;
-};
 
 namespace {
 
@@ -93,27 +58,6 @@ void free_buffers(tts_system *s)
     s->b = DevBuffers{};
 }
 
-template <typename T>
-int dev_alloc(T **ptr, size_t count, const char *what)
-{
-    void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        g_error = std::string("cudaMalloc of ") + what + " failed: " + cudaGetErrorString(e);
-        return TTS_ERR_OOM;
-    }
-    *ptr = static_cast<T *>(q);
-    return TTS_OK;
-}
-
-int upload(void *dst, const void *src, size_t bytes, cudaStream_t st, const char *what)
-{
-    if (bytes == 0) return TTS_OK;
-    TTS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), what);
-    TTS_CUDA(cudaStreamSynchronize(st), what);
-    return TTS_OK;
-}
 
 int validate(const tts_system_desc &d)
 {
@@ -158,7 +102,7 @@ struct HostTtm {
     std::vector<double> shape;
 };
 
-int make_host_ttm(const tts_system_desc &d, const HostInstance &hi, const tts_ttm_desc &t, double fwhm, HostTtm *o)
+int make_host_ttm(double step_dt, const HostInstance &hi, const tts_ttm_desc &t, double fwhm, HostTtm *o)
 {
     int resolved = 0;
     double dxmin = 0.0;
@@ -175,7 +119,7 @@ int make_host_ttm(const tts_system_desc &d, const HostInstance &hi, const tts_tt
     o->substeps = 1;
     if (resolved > 0 && t.kappa_e > 0.0) {
         const double limit = 0.4 * t.gamma_e * t.T0 * dxmin * dxmin / (t.kappa_e * resolved);
-        const double m = std::ceil(d.dt / limit);
+        const double m = std::ceil(step_dt / limit);
         o->substeps = m < 1.0 ? 1 : static_cast<int>(m);
     }
     o->sigma_t = fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
@@ -197,57 +141,6 @@ int make_host_ttm(const tts_system_desc &d, const HostInstance &hi, const tts_tt
                 }
             }
     return TTS_OK;
-}
-
-// Largest T_e over cells and step times of a TTM-only run with source power P0.
-double ttm_peak(const tts_system_desc &d, const tts_ttm_desc &t, const HostTtm &h, double P0)
-{
-    const int nx = h.cells[0], ny = h.cells[1], nz = h.cells[2], nc = nx * ny * nz;
-    std::vector<double> Te(nc, t.T0), Tl(nc, t.T0), dE(nc);
-    const int64_t nsteps = static_cast<int64_t>(std::ceil((h.t0 + 10.0 * h.sigma_t) / d.dt));
-    const double delta = d.dt / h.substeps;
-    double peak = t.T0;
-    for (int64_t n = 0; n < nsteps; ++n) {
-        for (int k = 0; k < h.substeps; ++k) {
-            const double tt = double(n) * d.dt + double(k) * delta;
-            const double z = (tt - h.t0) / h.sigma_t;
-            const double pulse = P0 * std::exp(-0.5 * z * z);
-            for (int cz = 0; cz < nz; ++cz)
-                for (int cy = 0; cy < ny; ++cy)
-                    for (int cx = 0; cx < nx; ++cx) {
-                        const int c = (cz * ny + cy) * nx + cx;
-                        double lap = 0.0;
-                        if (nx > 1)
-                            lap += (Te[(cz * ny + cy) * nx + (cx + 1) % nx] - 2.0 * Te[c] +
-                                    Te[(cz * ny + cy) * nx + (cx + nx - 1) % nx]) / (h.dx[0] * h.dx[0]);
-                        if (ny > 1)
-                            lap += (Te[(cz * ny + (cy + 1) % ny) * nx + cx] - 2.0 * Te[c] +
-                                    Te[(cz * ny + (cy + ny - 1) % ny) * nx + cx]) / (h.dx[1] * h.dx[1]);
-                        if (nz > 1)
-                            lap += (Te[(((cz + 1) % nz) * ny + cy) * nx + cx] - 2.0 * Te[c] +
-                                    Te[(((cz + nz - 1) % nz) * ny + cy) * nx + cx]) / (h.dx[2] * h.dx[2]);
-                        const double x = t.G * (Te[c] - Tl[c]);
-                        dE[c] = delta * (t.kappa_e * lap - x + pulse * h.shape[c]);
-                        Tl[c] += delta * x / t.C_l;
-                    }
-            for (int c = 0; c < nc; ++c) Te[c] = std::sqrt(2.0 * (0.5 * t.gamma_e * Te[c] * Te[c] + dE[c]) / t.gamma_e);
-        }
-        for (int c = 0; c < nc; ++c) peak = std::max(peak, Te[c]);
-    }
-    return peak;
-}
-
-double calibrate_P0(const tts_system_desc &d, const tts_ttm_desc &t, const HostTtm &h, double target)
-{
-    const double need = 0.5 * t.gamma_e * (target * target - t.T0 * t.T0);
-    double hi = need / (h.sigma_t * std::sqrt(2.0 * M_PI));
-    while (ttm_peak(d, t, h, hi) < target) hi *= 2.0;
-    double lo = 0.0;
-    for (int it = 0; it < 60; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (ttm_peak(d, t, h, mid) < target) lo = mid; else hi = mid;
-    }
-    return 0.5 * (lo + hi);
 }
 
 // ---------------------------------------------------------------------------
@@ -316,6 +209,7 @@ int alloc_cells(tts_system *s, int ncells_total)
     if ((rc = dev_alloc(&sig, size_t(ncells_total) * TTS_MAX_SPECIES * 2 * s->rsize, "sigma table"))) return rc;
     b.sigma = sig;
     s->ncells_total = ncells_total;
+    s->p.ncells_total = ncells_total;
     return TTS_OK;
 }
 
@@ -324,7 +218,9 @@ int alloc_cells(tts_system *s, int ncells_total)
 cudaError_t record_step(tts_system *s, cudaStream_t c, int *kernels, cudaEvent_t ev0, cudaEvent_t ev1)
 {
     *kernels = 0;
+    if (s->lat) return lattice_record_step(s, c, kernels, ev0, ev1);
     if (s->eng) return engine_record_step(s->eng, s->p, s->b, s->tp, s->ttm_active, c, kernels, ev0, ev1);
+    // general engine
     cudaError_t e = launch_sigma(s->p, s->b, s->ncells_total, s->precision, c);
     ++*kernels;
     if (e == cudaSuccess && ev0) e = cudaEventRecord(ev0, c);
@@ -375,6 +271,7 @@ void drop_profile_events(tts_system *s)
 {
     for (cudaEvent_t ev : s->prof_events) cudaEventDestroy(ev);
     s->prof_events.clear();
+    s->prof_pair_steps.clear();
 }
 
 int check_inst(tts_system *s, int inst)
@@ -389,10 +286,11 @@ int read_instance_spins(tts_system *s, int inst, double *out)
 {
     const DevInstance &di = s->dinst[inst];
     std::vector<R> x(di.n), y(di.n), z(di.n);
-    if (s->eng) {
-        int rc = engine_read_spins(s->eng, inst, x.data(), y.data(), z.data(), s->stream);
-        if (rc) return fail(rc, "engine spin read failed");
-    } else {
+    {
+        if (s->eng) {
+            cudaError_t e = engine_sync_to_general(s->eng, s->b, s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "engine gather");
+        }
         const size_t off = di.slot_begin * sizeof(R);
         TTS_CUDA(cudaMemcpyAsync(x.data(), static_cast<char *>(s->b.sx) + off, di.n * sizeof(R), cudaMemcpyDeviceToHost, s->stream), "read spins");
         TTS_CUDA(cudaMemcpyAsync(y.data(), static_cast<char *>(s->b.sy) + off, di.n * sizeof(R), cudaMemcpyDeviceToHost, s->stream), "read spins");
@@ -423,14 +321,18 @@ int write_instance_spins(tts_system *s, int inst, const double *in)
         z[so[a]] = static_cast<R>(vz / m);
     }
     if (s->eng) {
-        int rc = engine_write_spins(s->eng, inst, x.data(), y.data(), z.data(), s->stream);
-        if (rc) return fail(rc, "engine spin write failed");
-        return TTS_OK;
+        // bring the general arrays up to date first: only this instance is overwritten below
+        cudaError_t e = engine_sync_to_general(s->eng, s->b, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "engine gather");
     }
     const size_t off = di.slot_begin * sizeof(R);
     TTS_CUDA(cudaMemcpyAsync(static_cast<char *>(s->b.sx) + off, x.data(), di.n * sizeof(R), cudaMemcpyHostToDevice, s->stream), "write spins");
     TTS_CUDA(cudaMemcpyAsync(static_cast<char *>(s->b.sy) + off, y.data(), di.n * sizeof(R), cudaMemcpyHostToDevice, s->stream), "write spins");
     TTS_CUDA(cudaMemcpyAsync(static_cast<char *>(s->b.sz) + off, z.data(), di.n * sizeof(R), cudaMemcpyHostToDevice, s->stream), "write spins");
+    if (s->eng) {
+        cudaError_t e = engine_sync_from_general(s->eng, s->b, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "engine scatter");
+    }
     TTS_CUDA(cudaStreamSynchronize(s->stream), "write spins");
     return TTS_OK;
 }
@@ -451,6 +353,7 @@ int tts_destroy(tts_system *s)
     if (s->graph) cudaGraphExecDestroy(s->graph);
     drop_profile_events(s);
     if (s->eng) engine_destroy(s->eng);
+    if (s->lat) lattice_destroy(s->lat);
     free_buffers(s);
     if (s->capture) cudaStreamDestroy(s->capture);
     delete s;
@@ -587,6 +490,8 @@ int tts_create_system(const tts_system_desc *desc, void *stream, tts_system **ou
     p.instance_base = desc->instance_base;
     p.sample_every = desc->sample_every;
     p.obs_capacity = s->obs_capacity;
+    p.ncells_total = s->n_inst;
+    p.obs_blocks = s->obs_blocks;
 
     // engine choice
     s->engine = TTS_ENGINE_GENERAL;
@@ -683,34 +588,33 @@ int tts_set_ttm_grid(tts_system *s, const tts_ttm_desc *t)
     std::vector<double> shape(total), Te(total, t->T0);
     std::vector<int> cellmap(s->n_total);
     s->P0.assign(s->n_inst, t->P0);
-    // calibrations shared by instances with equal box, grid and pulse
-    struct Cal { double box[3], peak, fwhm, P0; };
-    std::vector<Cal> cache;
+    // calibration jobs: one per distinct (box, peak, pulse width); the jobs run
+    // on the GPU, one CTA each
+    struct CalKey { double box[3], peak, fwhm; };
+    std::vector<CalKey> keys;
+    std::vector<int> job_of(s->n_inst, -1);
+    std::vector<HostTtm> hts(s->n_inst);
     for (int i = 0; i < s->n_inst; ++i) {
         const HostInstance &hi = s->host[i];
         DevInstance &di = s->dinst[i];
         const double my_fwhm = s->inst_fwhm.empty() ? t->fwhm : s->inst_fwhm[i];
         const double my_peak = s->inst_peak.empty() ? t->peak_Te : s->inst_peak[i];
         if (t->source != TTS_SOURCE_NONE && !(my_fwhm > 0.0)) return fail(TTS_ERR_ARG, "pulse FWHM must be positive");
-        HostTtm h;
-        make_host_ttm(s->desc, hi, *t, my_fwhm, &h);
-        double P0 = t->P0;
+        HostTtm &h = hts[i];
+        make_host_ttm(lattice_step_length(s), hi, *t, t->source != TTS_SOURCE_NONE ? my_fwhm : 1.0, &h);
         if (t->source == TTS_SOURCE_PEAK) {
             if (!(my_peak > t->T0)) return fail(TTS_ERR_ARG, "peak T_e must exceed T0");
-            bool hit = false;
-            for (const Cal &c : cache)
-                if (c.box[0] == hi.box[0] && c.box[1] == hi.box[1] && c.box[2] == hi.box[2] && c.peak == my_peak &&
-                    c.fwhm == my_fwhm) {
-                    P0 = c.P0;
-                    hit = true;
-                    break;
-                }
-            if (!hit) {
-                P0 = calibrate_P0(s->desc, *t, h, my_peak);
-                cache.push_back({{hi.box[0], hi.box[1], hi.box[2]}, my_peak, my_fwhm, P0});
+            // a one-cell grid has no length scale: its calibration ignores the box
+            const double kb[3] = {nc > 1 ? hi.box[0] : 0.0, nc > 1 ? hi.box[1] : 0.0, nc > 1 ? hi.box[2] : 0.0};
+            for (size_t k = 0; k < keys.size(); ++k)
+                if (keys[k].box[0] == kb[0] && keys[k].box[1] == kb[1] && keys[k].box[2] == kb[2] &&
+                    keys[k].peak == my_peak && keys[k].fwhm == my_fwhm)
+                    job_of[i] = static_cast<int>(k);
+            if (job_of[i] < 0) {
+                job_of[i] = static_cast<int>(keys.size());
+                keys.push_back({{kb[0], kb[1], kb[2]}, my_peak, my_fwhm});
             }
         }
-        s->P0[i] = P0;
         di.cell_begin = i * nc;
         di.ncells = nc;
         for (int k = 0; k < 3; ++k) {
@@ -719,7 +623,7 @@ int tts_set_ttm_grid(tts_system *s, const tts_ttm_desc *t)
         }
         di.cell_volume = h.vol;
         di.substeps = h.substeps;
-        di.P0 = P0;
+        di.P0 = t->P0;
         di.sigma_t = h.sigma_t;
         di.t0 = h.t0;
         for (int c = 0; c < nc; ++c) shape[di.cell_begin + c] = h.shape[c];
@@ -731,6 +635,68 @@ int tts_set_ttm_grid(tts_system *s, const tts_ttm_desc *t)
             cellmap[di.slot_begin + s->slot_of_atom[i][a]] = di.cell_begin + (cc[2] * t->cells[1] + cc[1]) * t->cells[0] + cc[0];
         }
     }
+    TtmParams tp{};
+    tp.active = 1;
+    tp.gamma_e = t->gamma_e;
+    tp.C_l = t->C_l;
+    tp.G = t->G;
+    tp.kappa_e = t->kappa_e;
+    tp.T0 = t->T0;
+    tp.source = t->source;
+    tp.spatial = t->spatial;
+    tp.sigma_xy = t->sigma_xy;
+    tp.depth_z = t->depth_z;
+    if (!keys.empty()) {
+        const int nj = static_cast<int>(keys.size());
+        std::vector<int> first(nj, -1);
+        for (int i = 0; i < s->n_inst; ++i)
+            if (job_of[i] >= 0 && first[job_of[i]] < 0) first[job_of[i]] = i;
+        std::vector<CalibJob> jobs(nj);
+        double *shape_dev = nullptr, *work_dev = nullptr;
+        CalibJob *jobs_dev = nullptr;
+        if ((rc = dev_alloc(&shape_dev, size_t(nj) * nc, "calibration shapes")) ||
+            (rc = dev_alloc(&work_dev, size_t(nj) * 3 * nc, "calibration scratch")) ||
+            (rc = dev_alloc(&jobs_dev, nj, "calibration jobs"))) {
+            cudaFree(shape_dev);
+            cudaFree(work_dev);
+            return rc;
+        }
+        for (int j = 0; j < nj; ++j) {
+            const HostTtm &h = hts[first[j]];
+            CalibJob &J = jobs[j];
+            std::memset(&J, 0, sizeof J);
+            for (int k = 0; k < 3; ++k) {
+                J.cells[k] = h.cells[k];
+                J.dx[k] = h.dx[k];
+            }
+            J.substeps = h.substeps;
+            J.sigma_t = h.sigma_t;
+            J.t0 = h.t0;
+            J.target = keys[j].peak;
+            J.guess = 0.5 * t->gamma_e * (keys[j].peak * keys[j].peak - t->T0 * t->T0) /
+                      (h.sigma_t * std::sqrt(2.0 * M_PI));
+            J.nsteps = static_cast<int64_t>(std::ceil((h.t0 + 10.0 * h.sigma_t) / lattice_step_length(s)));
+            J.shape = shape_dev + size_t(j) * nc;
+            J.work = work_dev + size_t(j) * 3 * nc;
+            cudaMemcpyAsync(shape_dev + size_t(j) * nc, h.shape.data(), nc * sizeof(double), cudaMemcpyHostToDevice,
+                            s->stream);
+        }
+        cudaMemcpyAsync(jobs_dev, jobs.data(), nj * sizeof(CalibJob), cudaMemcpyHostToDevice, s->stream);
+        cudaError_t e = launch_calibrate(jobs_dev, nj, nc, lattice_step_length(s), tp, s->stream);
+        ++s->launches;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(jobs.data(), jobs_dev, nj * sizeof(CalibJob), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        cudaFree(shape_dev);
+        cudaFree(work_dev);
+        cudaFree(jobs_dev);
+        if (e != cudaSuccess) return cuda_fail(e, "source calibration");
+        for (int i = 0; i < s->n_inst; ++i)
+            if (job_of[i] >= 0) {
+                s->P0[i] = jobs[job_of[i]].P0;
+                s->dinst[i].P0 = s->P0[i];
+            }
+    }
     DevBuffers &b = s->b;
     if ((rc = upload(b.Te, Te.data(), total * sizeof(double), s->stream, "upload T_e"))) return rc;
     if ((rc = upload(b.Tl, Te.data(), total * sizeof(double), s->stream, "upload T_l"))) return rc;
@@ -739,20 +705,27 @@ int tts_set_ttm_grid(tts_system *s, const tts_ttm_desc *t)
     if ((rc = upload(b.inst, s->dinst.data(), s->dinst.size() * sizeof(DevInstance), s->stream, "upload instances"))) return rc;
     TTS_CUDA(cudaMemsetAsync(b.src_energy, 0, s->n_inst * sizeof(double), s->stream), "zero energy");
     TTS_CUDA(cudaStreamSynchronize(s->stream), "set ttm");
-    s->tp.active = 1;
-    s->tp.gamma_e = t->gamma_e;
-    s->tp.C_l = t->C_l;
-    s->tp.G = t->G;
-    s->tp.kappa_e = t->kappa_e;
-    s->tp.T0 = t->T0;
-    s->tp.source = t->source;
-    s->tp.spatial = t->spatial;
-    s->tp.sigma_xy = t->sigma_xy;
-    s->tp.depth_z = t->depth_z;
+    s->tp = tp;
     s->ttm_active = true;
+    if (s->lat) {
+        // bath cells from the current positions; ion energy tallies per cell
+        if ((rc = lattice_ensure_cell_acc(s)) || (rc = lattice_refresh_now(s))) return rc;
+    }
     if (s->eng) {
         rc = engine_set_cells(s->eng, s->dinst, cellmap, s->stream);
-        if (rc) return fail(rc, std::string("engine TTM set-up failed: ") + engine_last_error());
+        if (rc) {
+            if (s->desc.engine != TTS_ENGINE_AUTO)
+                return fail(rc, std::string("engine TTM set-up failed: ") + engine_last_error());
+            // AUTO: the general arrays hold the spins of a resident system, so
+            // the next valid engine can take over directly
+            engine_destroy(s->eng);
+            s->eng = nullptr;
+            s->engine = TTS_ENGINE_GENERAL;
+            if (engine_select(s->desc, s->host, TTS_ENGINE_CHECKER) == TTS_ENGINE_CHECKER &&
+                engine_create(s->desc, s->host, s->slot_of_atom, s->dinst, s->p, s->b, TTS_ENGINE_CHECKER, s->stream,
+                              &s->eng) == TTS_OK)
+                s->engine = TTS_ENGINE_CHECKER;
+        }
     }
     s->dirty = true;
     return TTS_OK;
@@ -763,6 +736,22 @@ int tts_step(tts_system *s, int64_t nsteps)
     if (!s) return fail(TTS_ERR_ARG, "null system");
     if (nsteps < 0) return fail(TTS_ERR_ARG, "nsteps must be >= 0");
     if (nsteps == 0) return TTS_OK;
+    if (s->eng && engine_multi_step(s->eng)) {
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        if (s->profiling) {
+            TTS_CUDA(cudaEventCreate(&ev[0]), "profile event");
+            TTS_CUDA(cudaEventCreate(&ev[1]), "profile event");
+            s->prof_events.push_back(ev[0]);
+            s->prof_events.push_back(ev[1]);
+            s->prof_pair_steps.push_back(nsteps);
+        }
+        int kernels = 0;
+        cudaError_t e = engine_run_steps(s->eng, s->p, s->b, s->tp, s->ttm_active, nsteps, s->stream, &kernels,
+                                         ev[0], ev[1]);
+        if (e != cudaSuccess) return cuda_fail(e, "resident steps");
+        s->launches += kernels;
+        return TTS_OK;
+    }
     if (s->profiling) {
         for (int64_t i = 0; i < nsteps; ++i) {
             cudaEvent_t ev[2];
@@ -770,6 +759,7 @@ int tts_step(tts_system *s, int64_t nsteps)
             TTS_CUDA(cudaEventCreate(&ev[1]), "profile event");
             s->prof_events.push_back(ev[0]);
             s->prof_events.push_back(ev[1]);
+            s->prof_pair_steps.push_back(1);
             int kernels = 0;
             cudaError_t e = record_step(s, s->stream, &kernels, ev[0], ev[1]);
             if (e != cudaSuccess) return cuda_fail(e, "profiled step");
@@ -805,12 +795,12 @@ int tts_profile_read(tts_system *s, double *ms, int64_t *steps, int64_t *spin_st
         float t = 0.0f;
         TTS_CUDA(cudaEventElapsedTime(&t, s->prof_events[k], s->prof_events[k + 1]), "profile elapsed");
         s->prof_ms += t;
-        s->prof_steps += 1;
+        s->prof_steps += s->prof_pair_steps[k / 2];
     }
     drop_profile_events(s);
     if (ms) *ms = s->prof_ms;
     if (steps) *steps = s->prof_steps;
-    if (spin_steps) *spin_steps = s->prof_steps * s->n_total;
+    if (spin_steps) *spin_steps = s->prof_steps * lattice_units_per_step(s);
     return TTS_OK;
 }
 
@@ -822,6 +812,9 @@ int tts_sync(tts_system *s)
     TTS_CUDA(cudaMemcpy(&h, s->b.health, sizeof h, cudaMemcpyDeviceToHost), "read health");
     if (h & kHealthTimeout) return fail(TTS_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out");
     if (h & kHealthNonFinite) return fail(TTS_ERR_HEALTH, "non-finite spin produced on the device");
+    if (h & kHealthSkin) return fail(TTS_ERR_HEALTH, "an atom moved further than half the skin from its site");
+    if (h & kHealthColour) return fail(TTS_ERR_HEALTH, "two exchange-coupled atoms share a colour class");
+    if (h & kHealthOverflow) return fail(TTS_ERR_HEALTH, "more exchange neighbours than the table holds");
     return TTS_OK;
 }
 

@@ -137,3 +137,39 @@ def cluster(positions, J, rc, mu=2.0, B=(0.0, 0.0, 0.0), T=0.0, alpha=0.0, dt=0.
         "init_dir": [list(init) if init is not None else [0.0, 0.0, 1.0]], "seed": seed,
         "sample_every": 0,
     }
+
+
+AMU = 1.66053906660e-27
+KB = 1.380649e-23
+
+
+def morse_fe_lattice(spin_substeps=10, strain_amp=0.005, T_init=300.0, gamma_p=None, G=1.7e18, a=2.8665):
+    """Moving-lattice block for bcc Fe: Morse pair potential (D = 0.4174 eV,
+    alpha = 1.3885 1/A, r0 = 2.845 A, cutoff 5 A), 10 spin steps per lattice
+    step, an initial sinusoidal strain along z and Maxwell-Boltzmann velocities.
+    The electron-ion friction defaults to gamma_p = G m / (3 n_a k_B) with
+    n_a = 2 / a^3 (the coefficient that reproduces a volumetric coupling G)."""
+    m = 55.845 * AMU
+    n_a = 2.0 / (a * 1e-10) ** 3
+    if gamma_p is None:
+        gamma_p = G * m / (3.0 * n_a * KB)
+    return {"mass_amu": 55.845, "morse_D": 0.4174 * EV, "morse_alpha": 1.3885, "morse_r0": 2.845,
+            "morse_rc": 5.0, "spin_substeps": spin_substeps, "strain_amp": strain_amp, "T_init": T_init,
+            "gamma_p": gamma_p}
+
+
+def ttm_z_exp(cells=(10, 10, 40), peak_Te=1500.0, fwhm=100 * FS, depth_frac=0.25, Lz=None, kappa_e=91.0):
+    """TTM grid with a source decaying into the depth z (exp(-z / depth))."""
+    return {"cells": list(cells), "gamma_e": 225.0, "C_l": 3.1e6, "G": 1.7e18, "kappa_e": kappa_e,
+            "T0": 300.0, "source": "peak", "peak_Te": peak_Te, "fwhm": fwhm, "spatial": "z_exp",
+            "depth_z": depth_frac * Lz}
+
+
+def config_moving_fe(n=40):
+    """Moving-lattice bcc Fe, n^3 cells, spin parameters of the bcc-Fe workload,
+    Morse lattice, 1 fs lattice step with 10 spin sub-steps of 0.1 fs, TTM
+    10x10x40 with a 100 fs pulse absorbed along z."""
+    s = bcc_fe(n)
+    lat = morse_fe_lattice()
+    ttm = ttm_z_exp((10, 10, 40), 1500.0, 100 * FS, 0.25, Lz=n * 2.8665)
+    return s, ttm, lat
