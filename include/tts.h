@@ -238,6 +238,20 @@ TTS_API int tts_set_spins(tts_system *sys, int inst, const double *host_xyz);
 TTS_API int tts_get_all_spins(tts_system *sys, double *host_xyz);
 TTS_API int tts_set_all_spins(tts_system *sys, const double *host_xyz);
 
+/* Bulk spin I/O for a host that keeps the state between calls: the spins of
+ * all instances, concatenated in instance order and canonical atom order,
+ * xyz interleaved, in the system's precision (float for a precision-32
+ * system, double for 64); bytes = 3 n_total (4 or 8).  The reordering runs on
+ * the device and the copy is one DMA on the system's stream: both calls
+ * return once queued, and host_xyz (page-locked memory gives full speed) must
+ * stay untouched until the stream reaches the copy (tts_sync).  Written spins
+ * are taken as given (not renormalised).  A device staging buffer of the same
+ * size is allocated at the first call and kept.
+ * Errors: TTS_ERR_ARG (null pointer, wrong byte count), TTS_ERR_OOM,
+ * TTS_ERR_CUDA. */
+TTS_API int tts_read_spins_async(tts_system *sys, void *host_xyz, size_t bytes);
+TTS_API int tts_write_spins_async(tts_system *sys, const void *host_xyz, size_t bytes);
+
 /* Atom count, species (int per atom) and colour class (int per atom) of one
  * instance, canonical order. */
 TTS_API int tts_instance_size(tts_system *sys, int inst, int64_t *n_atoms, int *n_colours);
@@ -311,6 +325,23 @@ TTS_API int tts_profile_read(tts_system *sys, double *ms, int64_t *steps, int64_
  * Errors: TTS_ERR_ARG, TTS_ERR_CUDA, TTS_ERR_UNSUPPORTED (device index > 63). */
 TTS_API int tts_ttm_advance_noalloc(const tts_ttm_desc *t, const double box_ang[3], double dt, int64_t step,
                                     double *dev_Te, double *dev_Tl, double *dev_deposited, void *stream);
+
+/* Autotuner: time every launch configuration the system's engine offers
+ * (block shapes of the colour-pass kernels; threads per CTA of the resident
+ * kernel) over probe_steps steps each, starting every probe from the same
+ * saved state and restoring it afterwards, and keep the fastest.  Choices are
+ * cached per engine, precision and shape for the life of the process.
+ * *chosen (may be NULL) receives the index of the configuration kept and
+ * *n_configs the number offered.  Results of later steps do not depend on the
+ * choice.  Errors: TTS_ERR_ARG, TTS_ERR_STATE (profiling on), TTS_ERR_CUDA. */
+TTS_API int tts_autotune(tts_system *sys, int probe_steps, int *chosen, int *n_configs);
+
+/* Select launch configuration `index` (0 .. n_configs - 1, the order the
+ * autotuner tries them; 0 is the engine's default) without timing anything.
+ * index < 0 only reports: *n_configs (may be NULL) receives the number offered
+ * and *current (may be NULL) the index in use.  Results do not depend on the
+ * choice.  Errors: TTS_ERR_ARG (index out of range). */
+TTS_API int tts_set_config(tts_system *sys, int index, int *current, int *n_configs);
 
 /* Message of the calling thread's last failed call (never NULL). */
 TTS_API const char *tts_last_error(void);

@@ -106,6 +106,10 @@ _SIG = {
     "tts_info": [C.c_void_p, _P(tts_info_t)],
     "tts_profile_enable": [C.c_void_p, C.c_int],
     "tts_profile_read": [C.c_void_p, _P(C.c_double), _P(C.c_int64), _P(C.c_int64)],
+    "tts_autotune": [C.c_void_p, C.c_int, _P(C.c_int), _P(C.c_int)],
+    "tts_set_config": [C.c_void_p, C.c_int, _P(C.c_int), _P(C.c_int)],
+    "tts_read_spins_async": [C.c_void_p, C.c_void_p, C.c_size_t],
+    "tts_write_spins_async": [C.c_void_p, C.c_void_p, C.c_size_t],
     "tts_set_lattice": [C.c_void_p, _P(tts_lattice_desc)],
     "tts_get_positions": [C.c_void_p, C.c_int, _P(C.c_double)],
     "tts_get_velocities": [C.c_void_p, C.c_int, _P(C.c_double)],
@@ -309,6 +313,23 @@ class System:
         a = np.ascontiguousarray(s, dtype=np.float64).reshape(self.n_total, 3)
         _check(load().tts_set_all_spins(self._h, _dp(a)))
 
+    def read_spins_async(self, out):
+        """tts_read_spins_async into a C-contiguous (n_total, 3) array of the
+        system's precision (page-locked for full speed); valid after sync()."""
+        self._check_io(out)
+        _check(load().tts_read_spins_async(self._h, C.c_void_p(out.ctypes.data), C.c_size_t(out.nbytes)))
+
+    def write_spins_async(self, src):
+        """tts_write_spins_async from a C-contiguous (n_total, 3) array of the
+        system's precision; src must stay untouched until sync()."""
+        self._check_io(src)
+        _check(load().tts_write_spins_async(self._h, C.c_void_p(src.ctypes.data), C.c_size_t(src.nbytes)))
+
+    def _check_io(self, a):
+        dt = np.float32 if self.precision == 32 else np.float64
+        if a.dtype != dt or a.shape != (self.n_total, 3) or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("expected a C-contiguous (%d, 3) %s array" % (self.n_total, np.dtype(dt).name))
+
     def get_species(self, inst=0):
         out = np.empty(self.sizes[inst][0], dtype=np.int32)
         _check(load().tts_get_species(self._h, int(inst), _ip(out)))
@@ -375,6 +396,19 @@ class System:
         out = np.empty((self.sizes[inst][0], 3))
         _check(load().tts_get_velocities(self._h, int(inst), _dp(out)))
         return out
+
+    def autotune(self, probe_steps=20):
+        """tts_autotune: returns (chosen configuration, configurations offered)."""
+        c, n = C.c_int(), C.c_int()
+        _check(load().tts_autotune(self._h, int(probe_steps), C.byref(c), C.byref(n)))
+        return c.value, n.value
+
+    def set_config(self, index=-1):
+        """tts_set_config: select launch configuration `index` (-1: none);
+        returns (configuration in use, configurations offered)."""
+        c, n = C.c_int(), C.c_int()
+        _check(load().tts_set_config(self._h, int(index), C.byref(c), C.byref(n)))
+        return c.value, n.value
 
     def engine_now(self):
         """Engine in use now (it can change when a TTM grid is attached)."""

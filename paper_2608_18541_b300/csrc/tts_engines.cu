@@ -25,6 +25,8 @@
 
 #include "tts_engines.h"
 #include "tts_fastmath.cuh"
+#include "tts_bulk.cuh"
+#include "tts_pair.cuh"
 #include "tts_philox.cuh"
 
 namespace tts {
@@ -66,8 +68,7 @@ struct CheckerInst {
 
 template <typename R>
 struct CheckerArgs {
-    typename Vec4<R>::T *S;
-    const CheckerInst *ci;
+    typename Vec4<R>::T *S;      // all instances, general slot order
     const int *cell;             // general slot -> TTM cell
     const R *sigma;              // [cell][species][h]
     const int64_t *step;
@@ -76,52 +77,56 @@ struct CheckerArgs {
     R nx, ny, nz, Bx, By, Bz;
     R dt;
     uint32_t key0, key1;
-    int n_inst;
-    int64_t total;               // work items per pass (sum of nhalf)
+    uint32_t Lx, Ly, Lz, hx;     // shape shared by all instances
+    uint32_t nkx;                // blocks along the hx colour sites of a row
+    uint32_t nhalf;              // sites per colour
+    int64_t n_inst_sites;        // sites per instance
+    uint32_t inst_base;          // global id of instance 0
 };
 
-template <typename R>
-__global__ void __launch_bounds__(256) checker_pass_kernel(CheckerArgs<R> a, int colour, int hsel, int pass)
+// One colour pass, one site per thread.  Block (BX, BY) threads cover BX
+// consecutive colour sites of BY rows; grid (ceil(hx / BX) * ceil(Ly / BY),
+// Lz, instances).  All instances share one shape, so no per-thread index needs
+// a division.
+// At most 256 threads a block; in FP32 six blocks per SM (40 registers a
+// thread), so that 48 warps hide the neighbour-load latency.
+template <typename R, bool AXZ>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) checker_pass_kernel(CheckerArgs<R> a, int colour, int hsel, int pass)
 {
     using V = typename Vec4<R>::T;
-    const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (gid >= a.total) return;
-    int i = 0;
-    if (a.n_inst > 1) {
-        int lo = 0, hi = a.n_inst - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (a.ci[mid].prefix <= gid) lo = mid; else hi = mid - 1;
-        }
-        i = lo;
-    }
-    const CheckerInst &I = a.ci[i];
-    const uint32_t k = static_cast<uint32_t>(gid - I.prefix);
-    const uint32_t row = fast_div(k, I.div_hx);
-    const uint32_t kx = k - row * I.hx;
-    const uint32_t z = fast_div(row, I.div_Ly);
-    const uint32_t y = row - z * I.Ly;
-    const uint32_t x = 2 * kx + ((y + z + colour) & 1u);
-    const uint32_t zp = (z + 1 == I.Lz) ? 0 : z + 1, zm = (z == 0) ? I.Lz - 1 : z - 1;
-    const uint32_t yp = (y + 1 == I.Ly) ? 0 : y + 1, ym = (y == 0) ? I.Ly - 1 : y - 1;
+    // block index -> (row block, x block); the quotient is uniform over the block
+    const uint32_t yb = blockIdx.x / a.nkx;
+    const uint32_t kx = (blockIdx.x - yb * a.nkx) * blockDim.x + threadIdx.x;
+    const uint32_t y = yb * blockDim.y + threadIdx.y;
+    const uint32_t hx = a.hx, Ly = a.Ly, Lz = a.Lz;
+    if (y >= Ly || kx >= hx) return;
+    const uint32_t z = blockIdx.y;
+    const int inst = blockIdx.z;
+    V *S = a.S + int64_t(inst) * a.n_inst_sites;
+    const V *O = S + (colour ? 0 : a.nhalf);
+    V *Own = S + (colour ? a.nhalf : 0);
+    const uint32_t zp = (z + 1 == Lz) ? 0 : z + 1, zm = (z == 0) ? Lz - 1 : z - 1;
+    const uint32_t yp = (y + 1 == Ly) ? 0 : y + 1, ym = (y == 0) ? Ly - 1 : y - 1;
+    const uint32_t row = z * Ly + y;
+    const uint32_t par = (y + z + colour) & 1u;
+    const uint32_t x = 2 * kx + par;
+    // x neighbours: the other colour's sites kx and kx +- 1 (periodic in hx)
     uint32_t kxp, kxm;
-    if (x & 1u) {
-        kxp = (kx + 1 == I.hx) ? 0 : kx + 1;
+    if (par) {
+        kxp = (kx + 1 == hx) ? 0 : kx + 1;
         kxm = kx;
     } else {
         kxp = kx;
-        kxm = (kx == 0) ? I.hx - 1 : kx - 1;
+        kxm = (kx == 0) ? hx - 1 : kx - 1;
     }
-    const int64_t own_base = I.slot_begin + int64_t(colour) * I.nhalf;
-    const V *O = a.S + I.slot_begin + int64_t(1 - colour) * I.nhalf;
-    const uint32_t rz = z * I.Ly, rowhx = row * I.hx;
-    const V n0 = O[(zp * I.Ly + y) * I.hx + kx];
-    const V n1 = O[(zm * I.Ly + y) * I.hx + kx];
-    const V n2 = O[(rz + yp) * I.hx + kx];
-    const V n3 = O[(rz + ym) * I.hx + kx];
-    const V n4 = O[rowhx + kxp];
-    const V n5 = O[rowhx + kxm];
-    V own = a.S[own_base + k];
+    const uint32_t k = row * hx + kx;
+    const V n0 = O[(zp * Ly + y) * hx + kx];
+    const V n1 = O[(zm * Ly + y) * hx + kx];
+    const V n2 = O[(z * Ly + yp) * hx + kx];
+    const V n3 = O[(z * Ly + ym) * hx + kx];
+    const V n4 = O[row * hx + kxp];
+    const V n5 = O[row * hx + kxm];
+    V own = Own[k];
     const R htx = n0.x + n1.x + n2.x + n3.x + n4.x + n5.x;
     const R hty = n0.y + n1.y + n2.y + n3.y + n4.y + n5.y;
     const R htz = n0.z + n1.z + n2.z + n3.z + n4.z + n5.z;
@@ -130,25 +135,518 @@ __global__ void __launch_bounds__(256) checker_pass_kernel(CheckerArgs<R> a, int
     const R h1z = n0.w * n0.z + n1.w * n1.z + n2.w * n2.z + n3.w * n3.z + n4.w * n4.z + n5.w * n5.z;
     const int t = own.w != R(0) ? 1 : 0;
     const FastSpecies<R> sp = t ? a.sp[1] : a.sp[0];
-    const int64_t slot = own_base + k;
-    const R sig = a.sigma[(int64_t(a.cell[slot]) * TTS_MAX_SPECIES + t) * 2 + hsel];
+    const int *cell = a.cell + int64_t(inst) * a.n_inst_sites + (colour ? a.nhalf : 0);
+    const R sig = a.sigma[(cell[k] * TTS_MAX_SPECIES + t) * 2 + hsel];
     const R h = hsel ? a.dt : R(0.5) * a.dt;
     R sx = own.x, sy = own.y, sz = own.z;
     if (sig > R(0)) {
-        const uint32_t atom = (z * I.Ly + y) * I.Lx + x;
-        const u32x4 w = philox4x32_10(u32x4{atom, static_cast<uint32_t>(*a.step), static_cast<uint32_t>(pass),
-                                            I.inst_global},
-                                      a.key0, a.key1);
-        fast_update<R>(sx, sy, sz, htx, hty, htz, h1x, h1y, h1z, sp, a.nx, a.ny, a.nz, a.Bx, a.By, a.Bz, sig, &w, h);
+        const uint32_t atom = row * a.Lx + x;
+        const u32x4 w = philox4x32_10(
+            u32x4{atom, static_cast<uint32_t>(*a.step), static_cast<uint32_t>(pass), a.inst_base + inst}, a.key0,
+            a.key1);
+        fast_update<R, AXZ>(sx, sy, sz, htx, hty, htz, h1x, h1y, h1z, sp, a.nx, a.ny, a.nz, a.Bx, a.By, a.Bz, sig, &w,
+                            h);
     } else {
-        fast_update<R>(sx, sy, sz, htx, hty, htz, h1x, h1y, h1z, sp, a.nx, a.ny, a.nz, a.Bx, a.By, a.Bz, sig, nullptr,
-                       h);
+        fast_update<R, AXZ>(sx, sy, sz, htx, hty, htz, h1x, h1y, h1z, sp, a.nx, a.ny, a.nz, a.Bx, a.By, a.Bz, sig,
+                            nullptr, h);
     }
-    if (!(isfinite(sx) && isfinite(sy) && isfinite(sz))) atomicOr(a.health, kHealthNonFinite);
+    // a non-finite component makes the sum non-finite
+    if (!isfinite(sx + sy + sz)) atomicOr(a.health, kHealthNonFinite);
     own.x = sx;
     own.y = sy;
     own.z = sz;
-    a.S[slot] = own;
+    Own[k] = own;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 checkerboard engine on site pairs.  Rows y and y + Ly/2 of one colour
+// are paired lane-wise: per instance and colour, pair q = (z Ly/2 + y) hx + kx
+// (y < Ly/2) is stored as two 16-byte words in two planes,
+//   lo plane: (x_A, x_B, y_A, y_B)      hi plane: (z_A, z_B, w_A, w_B),
+// A = row y, B = row y + Ly/2, w = species flag.  The neighbours of a pair in
+// z and x are pairs in the same lane order, in y too except across the row
+// Ly/2 - 1 | 0 boundary, where lanes swap.  Every load is a ready f32x2
+// operand, so the whole update runs on the packed FP32 pipe.
+// ---------------------------------------------------------------------------
+struct PairArgs {
+    ulonglong2 *S;               // all instances: [inst][colour][lo | hi plane][pair]
+    const int *cell;             // general slot -> TTM cell
+    const float *sigma;          // [cell][species][h]
+    const int64_t *step;
+    unsigned int *health;
+    PairConsts k;
+    uint32_t key0, key1;
+    uint32_t Lx, Ly, Lz, hx, Ly2;
+    uint32_t nkx;                // blocks along the hx colour sites of a row
+    uint32_t nhalf;              // sites per colour
+    uint32_t npair;              // pairs per colour (nhalf / 2)
+    int64_t n_inst_sites;
+    uint32_t inst_base;
+    int noise;                   // some species has alpha > 0 (else sigma = 0 everywhere)
+    // TTM cell of a site from its coordinates, cell0 + inst cstride +
+    // (cz ncy + cy) ncx + cx with c_k = floor(k n_k / L_k); the host checks it
+    // against the cell map, else cell_formula = 0 and the map is read.
+    int cell_formula;
+    int cell0, cstride;
+    uint32_t ncx, ncy, ncz;
+    FastDiv dLx, dLy, dLz;
+};
+
+struct Pair4 {
+    f2 x, y, z, w;
+};
+
+__device__ __forceinline__ Pair4 load_pair(const ulonglong2 *lo, const ulonglong2 *hi, uint32_t q)
+{
+    const ulonglong2 a = lo[q], b = hi[q];
+    return Pair4{f2{a.x}, f2{a.y}, f2{b.x}, f2{b.y}};
+}
+
+__device__ __forceinline__ Pair4 swap_lanes(const Pair4 &n)
+{
+    return Pair4{f2_swap(n.x), f2_swap(n.y), f2_swap(n.z), f2_swap(n.w)};
+}
+
+__device__ __forceinline__ void add_neighbour(const Pair4 &n, f2 &htx, f2 &hty, f2 &htz, f2 &h1x, f2 &h1y, f2 &h1z)
+{
+    htx = htx + n.x;
+    hty = hty + n.y;
+    htz = htz + n.z;
+    h1x = fma2(n.w, n.x, h1x);
+    h1y = fma2(n.w, n.y, h1y);
+    h1z = fma2(n.w, n.z, h1z);
+}
+
+// Where a pair sits: instance, plane z, pair row y2 < Ly/2, colour site kx,
+// and the x parities of its two rows.
+struct PairSite {
+    int inst;
+    uint32_t z, y2, kx, parA, parB;
+};
+
+__device__ __forceinline__ PairSite make_site(const PairArgs &a, int inst, uint32_t z, uint32_t y2, uint32_t kx,
+                                              int colour)
+{
+    PairSite p;
+    p.inst = inst;
+    p.z = z;
+    p.y2 = y2;
+    p.kx = kx;
+    p.parA = (y2 + z + uint32_t(colour)) & 1u;
+    p.parB = p.parA ^ (a.Ly2 & 1u);
+    return p;
+}
+
+// Thermal directions of the pair (Philox counters: atom, step, pass, global
+// instance); independent of any loaded value.
+__device__ __forceinline__ void site_noise(const PairArgs &a, const PairSite &p, uint32_t step, int pass, f2 &g1,
+                                           f2 &g2, f2 &g3)
+{
+    const uint32_t ig = a.inst_base + uint32_t(p.inst);
+    const uint32_t atomA = (p.z * a.Ly + p.y2) * a.Lx + 2 * p.kx + p.parA;
+    const uint32_t atomB = (p.z * a.Ly + p.y2 + a.Ly2) * a.Lx + 2 * p.kx + p.parB;
+    pair_noise(u32x4{atomA, step, static_cast<uint32_t>(pass), ig}, u32x4{atomB, step, static_cast<uint32_t>(pass), ig},
+               a.key0, a.key1, a.k, g1, g2, g3);
+}
+
+// Neighbour sums of a pair from one z plane's tile of the other colour (rows
+// ry-1, ry, ry+1 of the tile hold pair rows y2-1, y2, y2+1) and the two
+// planes z +- 1 (row ry).  Sum order: z+1, z-1, y+1, y-1, x, x'.
+__device__ __forceinline__ void neighbour_sums(const PairSite &p, uint32_t hx, uint32_t Ly2, const ulonglong2 *Pz_lo,
+                                               const ulonglong2 *Pz_hi, const ulonglong2 *Pp_lo,
+                                               const ulonglong2 *Pp_hi, const ulonglong2 *Pm_lo,
+                                               const ulonglong2 *Pm_hi, uint32_t rp, uint32_t rm,
+                                               uint32_t r0, uint32_t ryp, uint32_t rym, f2 &htx, f2 &hty, f2 &htz,
+                                               f2 &h1x, f2 &h1y, f2 &h1z)
+{
+    const uint32_t kx = p.kx;
+    const uint32_t kxp = (kx + 1 == hx) ? 0 : kx + 1, kxm = (kx == 0) ? hx - 1 : kx - 1;
+    htx = hty = htz = h1x = h1y = h1z = f2{0};
+    add_neighbour(load_pair(Pp_lo, Pp_hi, rp + kx), htx, hty, htz, h1x, h1y, h1z);
+    add_neighbour(load_pair(Pm_lo, Pm_hi, rm + kx), htx, hty, htz, h1x, h1y, h1z);
+    {
+        Pair4 n = load_pair(Pz_lo, Pz_hi, ryp + kx);
+        if (p.y2 + 1 == Ly2) n = swap_lanes(n);     // pair row 0 with lanes swapped
+        add_neighbour(n, htx, hty, htz, h1x, h1y, h1z);
+    }
+    {
+        Pair4 n = load_pair(Pz_lo, Pz_hi, rym + kx);
+        if (p.y2 == 0) n = swap_lanes(n);           // pair row Ly/2 - 1 with lanes swapped
+        add_neighbour(n, htx, hty, htz, h1x, h1y, h1z);
+    }
+    // x neighbours: the other colour's sites kx and kx + 1 (odd x) or kx - 1
+    // (even x); with Ly/2 odd the two lanes differ in parity
+    add_neighbour(load_pair(Pz_lo, Pz_hi, r0 + kx), htx, hty, htz, h1x, h1y, h1z);
+    if (p.parA == p.parB) {
+        add_neighbour(load_pair(Pz_lo, Pz_hi, r0 + (p.parA ? kxp : kxm)), htx, hty, htz, h1x, h1y, h1z);
+    } else {
+        const Pair4 P = load_pair(Pz_lo, Pz_hi, r0 + kxp), M = load_pair(Pz_lo, Pz_hi, r0 + kxm);
+        const Pair4 &LA = p.parA ? P : M, &LB = p.parA ? M : P;
+        add_neighbour(Pair4{f2_mix(LA.x, LB.x), f2_mix(LA.y, LB.y), f2_mix(LA.z, LB.z), f2_mix(LA.w, LB.w)}, htx,
+                      hty, htz, h1x, h1y, h1z);
+    }
+}
+
+// Update the pair from its neighbour sums and own words and store it at pair
+// q of the own colour's planes.
+template <bool AXZ>
+__device__ __forceinline__ void pair_finish(const PairArgs &a, const PairSite &p, int colour, int hsel, f2 g1, f2 g2,
+                                            f2 g3, f2 htx, f2 hty, f2 htz, f2 h1x, f2 h1y, f2 h1z, ulonglong2 olo,
+                                            ulonglong2 ohi, ulonglong2 *Wlo, ulonglong2 *Whi, uint32_t q)
+{
+    f2 sx{olo.x}, sy{olo.y}, sz{ohi.x};
+    const f2 w{ohi.y};
+    f2 sig{0};
+    if (a.noise) {
+        float wA, wB;
+        f2_split(w, wA, wB);
+        const int tA = wA != 0.0f ? 1 : 0, tB = wB != 0.0f ? 1 : 0;
+        int cA, cB;
+        if (a.cell_formula) {
+            const uint32_t cz = fast_div(p.z * a.ncz, a.dLz);
+            const uint32_t cyA = fast_div(p.y2 * a.ncy, a.dLy), cyB = fast_div((p.y2 + a.Ly2) * a.ncy, a.dLy);
+            const uint32_t cxA = fast_div((2 * p.kx + p.parA) * a.ncx, a.dLx);
+            const uint32_t cxB = fast_div((2 * p.kx + p.parB) * a.ncx, a.dLx);
+            const int base = a.cell0 + p.inst * a.cstride;
+            cA = base + int((cz * a.ncy + cyA) * a.ncx + cxA);
+            cB = base + int((cz * a.ncy + cyB) * a.ncx + cxB);
+        } else {
+            // general slots of the two sites within the instance
+            const uint32_t slotA = uint32_t(colour) * a.nhalf + (p.z * a.Ly + p.y2) * a.hx + p.kx;
+            const uint32_t slotB = slotA + a.Ly2 * a.hx;
+            const int *cell = a.cell + int64_t(p.inst) * a.n_inst_sites;
+            cA = cell[slotA];
+            cB = cell[slotB];
+        }
+        sig = f2_make(a.sigma[(cA * TTS_MAX_SPECIES + tA) * 2 + hsel], a.sigma[(cB * TTS_MAX_SPECIES + tB) * 2 + hsel]);
+    }
+    pair_update<AXZ>(sx, sy, sz, htx, hty, htz, h1x, h1y, h1z, w, a.noise != 0, sig, g1, g2, g3, a.k);
+    float sA, sB;
+    f2_split(sx + sy + sz, sA, sB);
+    // a non-finite component makes the sum non-finite
+    if (!isfinite(sA) || !isfinite(sB)) atomicOr(a.health, kHealthNonFinite);
+    Wlo[q] = ulonglong2{sx.v, sy.v};
+    Whi[q] = ulonglong2{sz.v, ohi.y};
+}
+
+// One colour pass, one site pair per thread, neighbours read from global
+// memory.  Block (BX, BY) covers BX consecutive pairs of BY pair rows; grid
+// (ceil(hx / BX) * ceil(Ly/2 / BY), Lz, instances).  Registers are capped at
+// 64 (four 256-thread blocks a SM); a budget of 85 with fewer threads in
+// flight measured slower.
+template <bool AXZ>
+__global__ void __launch_bounds__(256, 4) checker_pair_kernel(PairArgs a, int colour, int hsel, int pass)
+{
+    const uint32_t yb = blockIdx.x / a.nkx;
+    const uint32_t kx = (blockIdx.x - yb * a.nkx) * blockDim.x + threadIdx.x;
+    const uint32_t y2 = yb * blockDim.y + threadIdx.y;
+    const uint32_t hx = a.hx, Ly2 = a.Ly2, Lz = a.Lz;
+    if (y2 >= Ly2 || kx >= hx) return;
+    const uint32_t z = blockIdx.y;
+    const int inst = blockIdx.z;
+    const PairSite p = make_site(a, inst, z, y2, kx, colour);
+    f2 g1{0}, g2{0}, g3{0};
+    if (a.noise) site_noise(a, p, static_cast<uint32_t>(*a.step), pass, g1, g2, g3);
+    ulonglong2 *base = a.S + int64_t(inst) * a.n_inst_sites;
+    const ulonglong2 *Olo = base + (colour ? 0 : a.nhalf);
+    const ulonglong2 *Ohi = Olo + a.npair;
+    ulonglong2 *Wlo = base + (colour ? a.nhalf : 0);
+    ulonglong2 *Whi = Wlo + a.npair;
+    const uint32_t zp = (z + 1 == Lz) ? 0 : z + 1, zm = (z == 0) ? Lz - 1 : z - 1;
+    const uint32_t yp = (y2 + 1 == Ly2) ? 0 : y2 + 1, ym = (y2 == 0) ? Ly2 - 1 : y2 - 1;
+    const uint32_t r0 = (z * Ly2 + y2) * hx;
+    f2 htx, hty, htz, h1x, h1y, h1z;
+    neighbour_sums(p, hx, Ly2, Olo, Ohi, Olo, Ohi, Olo, Ohi, (zp * Ly2 + y2) * hx, (zm * Ly2 + y2) * hx, r0,
+                   (z * Ly2 + yp) * hx, (z * Ly2 + ym) * hx, htx, hty, htz, h1x, h1y, h1z);
+    const uint32_t q = r0 + kx;
+    pair_finish<AXZ>(a, p, colour, hsel, g1, g2, g3, htx, hty, htz, h1x, h1y, h1z, Wlo[q], Whi[q], Wlo, Whi, q);
+}
+
+// ---------------------------------------------------------------------------
+// The same pass with the other colour staged in shared memory by bulk copies.
+// A CTA owns a column of one instance -- pair rows [y0, y0 + BY) of every
+// colour site of the row (hx = Lx/2 a power of two, BY hx <= 256 threads) --
+// and marches along z over its share of the (column, z) planes, so that each
+// other-colour plane tile (rows y0 - 1 .. y0 + BY, wrapped in y) is copied
+// once and serves the planes z - 1, z and z + 1.  A ring of four tiles holds
+// z - 1, z, z + 1 while z + 2 is in flight; the own pairs of the next plane
+// are copied into a second ring of two.  Results go straight to global
+// memory (a site is read and written by its own thread only).
+// ---------------------------------------------------------------------------
+struct TileArgs {
+    uint32_t by;                 // pair rows per tile
+    uint32_t hx_shift;           // log2(hx)
+    uint32_t nyb;                // column blocks per instance (Ly/2 / by)
+    uint32_t ncol;               // columns over all instances
+    uint64_t units;              // ncol * Lz planes
+};
+
+constexpr uint64_t kBulkWaitNs = 1000000000ull;   // 1 s
+
+template <bool AXZ>
+__global__ void __launch_bounds__(256, 3) checker_pair_tiled_kernel(PairArgs a, TileArgs t, int colour, int hsel,
+                                                                    int pass)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_abort;
+    const uint32_t hx = a.hx, by = t.by, Ly2 = a.Ly2, Lz = a.Lz;
+    const uint32_t to = (by + 2) * hx;          // pairs of an other-colour tile
+    const uint32_t tw = by * hx;                // pairs of an own tile
+    ulonglong2 *oring = reinterpret_cast<ulonglong2 *>(smem);      // 4 x (lo to | hi to)
+    ulonglong2 *wring = oring + 8 * to;                             // 2 x (lo tw | hi tw)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(wring + 4 * tw);  // 4 other + 2 own
+    const uint32_t tid = threadIdx.x;
+    const uint32_t ty = tid >> t.hx_shift, tx = tid & (hx - 1);
+    const bool active = ty < by;
+    if (tid == 0) {
+        for (int i = 0; i < 6; ++i) mbar_init(bar + i, 1);
+        mbar_init_fence();
+        s_abort = 0;
+    }
+    __syncthreads();
+    const uint32_t step = static_cast<uint32_t>(*a.step);
+    const uint64_t u_begin = uint64_t(blockIdx.x) * t.units / gridDim.x;
+    const uint64_t u_end = uint64_t(blockIdx.x + 1) * t.units / gridDim.x;
+    const int other = 1 - colour;
+    uint32_t n_o = 0, n_w = 0;       // tiles issued into each ring so far (uniform)
+    uint32_t c_o = 0, c_w = 0;       // tiles consumed (uniform)
+    bool ok = true;
+    for (uint64_t u = u_begin; u < u_end && ok;) {
+        const uint32_t col = static_cast<uint32_t>(u / Lz);
+        const uint32_t za = static_cast<uint32_t>(u - uint64_t(col) * Lz);
+        const uint32_t zb = static_cast<uint32_t>(min(uint64_t(Lz), za + (u_end - u)));
+        const int inst = static_cast<int>(col / t.nyb);
+        const uint32_t y0 = (col - uint32_t(inst) * t.nyb) * by;
+        const ulonglong2 *gbase = a.S + int64_t(inst) * a.n_inst_sites;
+        const ulonglong2 *go = gbase + (other ? a.nhalf : 0);
+        ulonglong2 *gw = const_cast<ulonglong2 *>(gbase) + (colour ? a.nhalf : 0);
+        // thread 0: copy tile rows y0 - 1 .. y0 + by of other-colour plane zz
+        auto issue_other = [&](uint32_t zz) {
+            const uint32_t slot = n_o & 3u;
+            uint64_t *b = bar + slot;
+            ulonglong2 *dlo = oring + slot * 2 * to, *dhi = dlo + to;
+            mbar_arrive_expect_tx(b, 2u * to * 16u);
+            uint32_t r = 0;
+            while (r < by + 2) {
+                const uint32_t row = (y0 + Ly2 - 1 + r) % Ly2;
+                const uint32_t run = min(by + 2 - r, Ly2 - row);
+                const uint32_t src = (zz * Ly2 + row) * hx;
+                bulk_copy_g2s(dlo + r * hx, go + src, run * hx * 16u, b);
+                bulk_copy_g2s(dhi + r * hx, go + a.npair + src, run * hx * 16u, b);
+                r += run;
+            }
+            ++n_o;
+        };
+        auto issue_own = [&](uint32_t zz) {
+            const uint32_t slot = n_w & 1u;
+            uint64_t *b = bar + 4 + slot;
+            ulonglong2 *dlo = wring + slot * 2 * tw, *dhi = dlo + tw;
+            mbar_arrive_expect_tx(b, 2u * tw * 16u);
+            const uint32_t src = (zz * Ly2 + y0) * hx;
+            bulk_copy_g2s(dlo, gw + src, tw * 16u, b);
+            bulk_copy_g2s(dhi, gw + a.npair + src, tw * 16u, b);
+            ++n_w;
+        };
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            issue_other(za == 0 ? Lz - 1 : za - 1);
+            issue_other(za);
+            issue_other(za + 1 == Lz ? 0 : za + 1);
+            issue_own(za);
+        } else {
+            n_o += 3;
+            n_w += 1;
+        }
+        for (uint32_t z = za; z < zb; ++z) {
+            if (tid == 0) {
+                fence_proxy_async_smem();
+                if (z + 2 <= zb) issue_other((z + 2) % Lz);
+                if (z + 1 < zb) issue_own(z + 1);
+            } else {
+                if (z + 2 <= zb) ++n_o;
+                if (z + 1 < zb) ++n_w;
+            }
+            const PairSite p = make_site(a, inst, z, y0 + ty, tx, colour);
+            f2 g1{0}, g2{0}, g3{0};
+            if (active && a.noise) site_noise(a, p, step, pass, g1, g2, g3);
+            // tiles of planes z - 1, z, z + 1 (other) and z (own)
+            const uint32_t im = c_o, i0 = c_o + 1, ip = c_o + 2, iw = c_w;
+            bool got = mbar_wait(bar + (im & 3u), (im >> 2) & 1u, kBulkWaitNs) &&
+                       mbar_wait(bar + (i0 & 3u), (i0 >> 2) & 1u, kBulkWaitNs) &&
+                       mbar_wait(bar + (ip & 3u), (ip >> 2) & 1u, kBulkWaitNs) &&
+                       mbar_wait(bar + 4 + (iw & 1u), (iw >> 1) & 1u, kBulkWaitNs);
+            if (!got) {
+                atomicOr(a.health, kHealthTimeout);
+                s_abort = 1;
+            }
+            if (got && active) {
+                const ulonglong2 *Tm = oring + (im & 3u) * 2 * to, *T0 = oring + (i0 & 3u) * 2 * to,
+                                 *Tp = oring + (ip & 3u) * 2 * to, *Tw = wring + (iw & 1u) * 2 * tw;
+                f2 htx, hty, htz, h1x, h1y, h1z;
+                const uint32_t r1 = (ty + 1) * hx;
+                neighbour_sums(p, hx, Ly2, T0, T0 + to, Tp, Tp + to, Tm, Tm + to, r1, r1, r1, (ty + 2) * hx,
+                               ty * hx, htx, hty, htz, h1x, h1y, h1z);
+                const uint32_t qs = ty * hx + tx;
+                const uint32_t q = (z * Ly2 + y0 + ty) * hx + tx;
+                pair_finish<AXZ>(a, p, colour, hsel, g1, g2, g3, htx, hty, htz, h1x, h1y, h1z, Tw[qs], Tw[tw + qs],
+                                 gw, gw + a.npair, q);
+            }
+            ++c_o;
+            ++c_w;
+            __syncthreads();
+            if (s_abort) {
+                ok = false;
+                break;
+            }
+        }
+        if (ok) {
+            c_o += 2;          // the segment's last two tiles served as planes z and z + 1 of its last plane
+            u += zb - za;
+        }
+    }
+    // after a time-out: let this CTA's copies in flight land before exiting
+    if (!ok && tid == 0) {
+        for (uint32_t i = c_o - 1; i < n_o; ++i) mbar_wait(bar + (i & 3u), (i >> 2) & 1u, kBulkWaitNs);
+        for (uint32_t i = c_w - 1; i < n_w; ++i) mbar_wait(bar + 4 + (i & 1u), (i >> 1) & 1u, kBulkWaitNs);
+    }
+}
+
+// Observables of the pair layout: the same per-species partial sums, block
+// by block, as the general observable kernel.  Per site, in FP32 and tesla:
+// the unit-free terms 1, s, s.h, (s.n)^2, B.s, |s x B_tot|^2, s.B_tot (h the
+// exchange field, B_tot = h + kappa (s.n) n + B), summed over the thread's 8
+// sites; then scaled by mu and K of the species and summed in FP64.
+struct PairObsArgs {
+    const int *obs_block_inst;
+    const DevInstance *inst;
+    double *obs_partial;
+    int obs_blocks;
+    int sample_every;
+    double mu[TTS_MAX_SPECIES], K[TTS_MAX_SPECIES];
+};
+
+constexpr int kObsTerms = 9;
+
+__global__ void __launch_bounds__(kObsBlock) checker_pair_obs_kernel(PairArgs a, PairObsArgs o, int mode)
+{
+    const int64_t step = *a.step;
+    if (mode == 0 && (o.sample_every <= 0 || (step + 1) % o.sample_every != 0)) return;
+    const uint32_t hx = a.hx, Ly2 = a.Ly2, Lz = a.Lz;
+    const PairConsts &k = a.k;
+    for (int blk = blockIdx.x; blk < o.obs_blocks; blk += gridDim.x) {
+        const int inst = o.obs_block_inst[blk];
+        const uint32_t local = static_cast<uint32_t>(blk - o.inst[inst].obs_block_begin);
+        f2 c0[kObsTerms], c1[kObsTerms];
+#pragma unroll
+        for (int t = 0; t < kObsTerms; ++t) c0[t] = c1[t] = f2{0};
+        const ulonglong2 *base = a.S + int64_t(inst) * a.n_inst_sites;
+        for (int j = 0; j < kObsSpan / 2 / kObsBlock; ++j) {
+            const uint32_t P = local * (kObsSpan / 2) + threadIdx.x + uint32_t(j) * kObsBlock;
+            if (P >= 2 * a.npair) break;
+            const int colour = P >= a.npair ? 1 : 0;
+            const uint32_t q = P - uint32_t(colour) * a.npair;
+            const uint32_t zy = q / hx, kx = q - zy * hx;
+            const uint32_t z = zy / Ly2, y2 = zy - z * Ly2;
+            const PairSite ps = make_site(a, inst, z, y2, kx, colour);
+            const ulonglong2 *Olo = base + (colour ? 0 : a.nhalf), *Ohi = Olo + a.npair;
+            const ulonglong2 *Wlo = base + (colour ? a.nhalf : 0), *Whi = Wlo + a.npair;
+            const uint32_t zp = (z + 1 == Lz) ? 0 : z + 1, zm = (z == 0) ? Lz - 1 : z - 1;
+            const uint32_t yp = (y2 + 1 == Ly2) ? 0 : y2 + 1, ym = (y2 == 0) ? Ly2 - 1 : y2 - 1;
+            f2 htx, hty, htz, h1x, h1y, h1z;
+            neighbour_sums(ps, hx, Ly2, Olo, Ohi, Olo, Ohi, Olo, Ohi, (zp * Ly2 + y2) * hx, (zm * Ly2 + y2) * hx,
+                           zy * hx, (z * Ly2 + yp) * hx, (z * Ly2 + ym) * hx, htx, hty, htz, h1x, h1y, h1z);
+            const ulonglong2 lo = Wlo[q], hi = Whi[q];
+            const f2 sx{lo.x}, sy{lo.y}, sz{hi.x}, w{hi.y};
+            const f2 J0 = fma2(w, k.J0d, k.J0c), dJ = fma2(w, k.dJd, k.dJc), kap = fma2(w, k.kd, k.kc);
+            const f2 hX = fma2(J0, htx, dJ * h1x), hY = fma2(J0, hty, dJ * h1y), hZ = fma2(J0, htz, dJ * h1z);
+            const f2 sn = fma2(sz, k.nz, fma2(sy, k.ny, sx * k.nx));
+            const f2 ka = kap * sn;
+            const f2 Bx = fma2(ka, k.nx, hX + k.Bx), By = fma2(ka, k.ny, hY + k.By), Bz = fma2(ka, k.nz, hZ + k.Bz);
+            const f2 cx = sy * Bz - sz * By, cy = sz * Bx - sx * Bz, cz = sx * By - sy * Bx;
+            const f2 term[kObsTerms] = {k.one,
+                                        sx,
+                                        sy,
+                                        sz,
+                                        fma2(sz, hZ, fma2(sy, hY, sx * hX)),
+                                        sn * sn,
+                                        fma2(sz, k.Bz, fma2(sy, k.By, sx * k.Bx)),
+                                        fma2(cz, cz, fma2(cy, cy, cx * cx)),
+                                        fma2(sz, Bz, fma2(sy, By, sx * Bx))};
+            const f2 m0 = k.one - w;
+#pragma unroll
+            for (int t = 0; t < kObsTerms; ++t) {
+                c0[t] = fma2(m0, term[t], c0[t]);
+                c1[t] = fma2(w, term[t], c1[t]);
+            }
+        }
+        double acc[kObsFields];
+#pragma unroll
+        for (int f = 0; f < kObsFields; ++f) acc[f] = 0.0;
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp) {
+            double v[kObsTerms];
+#pragma unroll
+            for (int t = 0; t < kObsTerms; ++t) {
+                float l, h;
+                f2_split(sp ? c1[t] : c0[t], l, h);
+                v[t] = double(l) + double(h);
+            }
+            const double mu = o.mu[sp], K = o.K[sp];
+            double *q = acc + 12 * sp;
+            q[0] = v[0];
+            q[1] = v[1];
+            q[2] = v[2];
+            q[3] = v[3];
+            q[7] = -0.5 * mu * v[4];
+            q[8] = -K * v[5];
+            q[9] = -mu * v[6];
+            q[10] = mu * mu * v[7];
+            q[11] = mu * v[8];
+        }
+        block_sum_store<kObsFields>(acc, o.obs_partial + int64_t(blk) * kObsFields);
+    }
+}
+
+// pair planes <-> general SoA.  One thread per pair; general slot of a site
+// within its instance: colour * nhalf + (z Ly + y) hx + kx.
+__global__ void pair_to_general_kernel(const float4 *__restrict__ S, float *sx, float *sy, float *sz, int64_t npairs,
+                                       uint32_t hx, uint32_t Ly2, uint32_t npair, const int64_t *step,
+                                       int sample_every, int conditional)
+{
+    if (conditional && (sample_every <= 0 || (*step + 1) % sample_every != 0)) return;
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= npairs) return;
+    const int64_t block = g / npair;              // (instance, colour) block
+    const uint32_t q = static_cast<uint32_t>(g - block * npair);
+    const int64_t site0 = block * int64_t(2 * npair);   // first general slot of the block
+    const uint32_t zy = q / hx, kx = q - zy * hx;
+    const uint32_t z = zy / Ly2, y2 = zy - z * Ly2;
+    const int64_t iA = site0 + (int64_t(z) * 2 * Ly2 + y2) * hx + kx;
+    const int64_t iB = iA + int64_t(Ly2) * hx;
+    const float4 lo = S[site0 + q], hi = S[site0 + npair + q];
+    sx[iA] = lo.x;
+    sx[iB] = lo.y;
+    sy[iA] = lo.z;
+    sy[iB] = lo.w;
+    sz[iA] = hi.x;
+    sz[iB] = hi.y;
+}
+
+__global__ void pair_from_general_kernel(float4 *S, const float *__restrict__ sx, const float *__restrict__ sy,
+                                         const float *__restrict__ sz, const uint8_t *__restrict__ spc,
+                                         int64_t npairs, uint32_t hx, uint32_t Ly2, uint32_t npair)
+{
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= npairs) return;
+    const int64_t block = g / npair;
+    const uint32_t q = static_cast<uint32_t>(g - block * npair);
+    const int64_t site0 = block * int64_t(2 * npair);
+    const uint32_t zy = q / hx, kx = q - zy * hx;
+    const uint32_t z = zy / Ly2, y2 = zy - z * Ly2;
+    const int64_t iA = site0 + (int64_t(z) * 2 * Ly2 + y2) * hx + kx;
+    const int64_t iB = iA + int64_t(Ly2) * hx;
+    S[site0 + q] = make_float4(sx[iA], sx[iB], sy[iA], sy[iB]);
+    S[site0 + npair + q] = make_float4(sz[iA], sz[iB], spc[iA] ? 1.0f : 0.0f, spc[iB] ? 1.0f : 0.0f);
 }
 
 // general SoA <-> engine float4 (same slot order)
@@ -318,8 +816,46 @@ __device__ __noinline__ void resident_observe(const ResArgs<R> &a, const ResInst
     __syncthreads();
 }
 
+// Thread 0's FP64 work for one step, out of line so that it does not raise
+// the register count of the spin loop: the noise table of step `step` from
+// T_e (mode 0), or the one-cell TTM advance t_n -> t_n+1 (mode 1).
 template <typename R>
-__global__ void resident_kernel(ResArgs<R> a, int64_t nsteps)
+__device__ __noinline__ void resident_bath(const ResArgs<R> &a, const DevInstance &D, int64_t step, int mode,
+                                           double *T, double *deposited, R *sigma_out)
+{
+    if (mode == 0) {
+        for (int t = 0; t < TTS_MAX_SPECIES; ++t)
+            for (int hs = 0; hs < 2; ++hs) {
+                double v = 0.0;
+                if (t < a.nspecies && T[0] > 0.0 && a.spd[t].alpha > 0.0) {
+                    const double h = hs ? a.dt : 0.5 * a.dt;
+                    v = sqrt(2.0 * a.spd[t].alpha * kBoltzmann * T[0] / (kGyro * a.spd[t].mu * h));
+                }
+                sigma_out[t * 2 + hs] = static_cast<R>(v);
+            }
+        return;
+    }
+    double Te = T[0], Tl = T[1];
+    const double delta = a.dt / D.substeps;
+    for (int k = 0; k < D.substeps; ++k) {
+        const double tt = double(step) * a.dt + double(k) * delta;
+        double src = 0.0;
+        if (a.tp.source != TTS_SOURCE_NONE) {
+            const double zz = (tt - D.t0) / D.sigma_t;
+            src = D.P0 * exp(-0.5 * zz * zz);
+        }
+        const double xch = a.tp.G * (Te - Tl);
+        const double dE = delta * (-xch + src);
+        *deposited += delta * src * D.cell_volume;
+        Tl += delta * xch / a.tp.C_l;
+        Te = sqrt(2.0 * (0.5 * a.tp.gamma_e * Te * Te + dE) / a.tp.gamma_e);
+    }
+    T[0] = Te;
+    T[1] = Tl;
+}
+
+template <typename R, bool AXZ>
+__global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<R> a, int64_t nsteps)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     R *sx = reinterpret_cast<R *>(smem);
@@ -357,15 +893,8 @@ __global__ void resident_kernel(ResArgs<R> a, int64_t nsteps)
         for (int64_t st = 0; st < nsteps; ++st) {
             const int64_t step = step0 + st;
             if (threadIdx.x == 0) {
-                for (int t = 0; t < TTS_MAX_SPECIES; ++t)
-                    for (int hs = 0; hs < 2; ++hs) {
-                        double v = 0.0;
-                        if (t < a.nspecies && Te > 0.0 && a.spd[t].alpha > 0.0) {
-                            const double h = hs ? a.dt : 0.5 * a.dt;
-                            v = sqrt(2.0 * a.spd[t].alpha * kBoltzmann * Te / (kGyro * a.spd[t].mu * h));
-                        }
-                        s_sigma[t][hs] = static_cast<R>(v);
-                    }
+                double T[2] = {Te, Tl};
+                resident_bath<R>(a, D, step, 0, T, &deposited, &s_sigma[0][0]);
             }
             __syncthreads();
             const int K = I.ncolours;
@@ -403,13 +932,12 @@ __global__ void resident_kernel(ResArgs<R> a, int64_t nsteps)
                     const R sig = s_sigma[t][hsel];
                     if (sig > R(0)) {
                         const u32x4 w = philox4x32_10(
-                            u32x4{at, static_cast<uint32_t>(step), static_cast<uint32_t>(p), I.inst_global}, a.key0,
-                            a.key1);
-                        fast_update<R>(s0, s1, s2, htx, hty, htz, h1x, h1y, h1z, sp, R(a.axis[0]), R(a.axis[1]),
-                                       R(a.axis[2]), R(a.B[0]), R(a.B[1]), R(a.B[2]), sig, &w, h);
+                            u32x4{at, static_cast<uint32_t>(step), static_cast<uint32_t>(p), I.inst_global}, a.key0, a.key1);
+                        fast_update<R, AXZ>(s0, s1, s2, htx, hty, htz, h1x, h1y, h1z, sp, R(a.axis[0]), R(a.axis[1]),
+                                            R(a.axis[2]), R(a.B[0]), R(a.B[1]), R(a.B[2]), sig, &w, h);
                     } else {
-                        fast_update<R>(s0, s1, s2, htx, hty, htz, h1x, h1y, h1z, sp, R(a.axis[0]), R(a.axis[1]),
-                                       R(a.axis[2]), R(a.B[0]), R(a.B[1]), R(a.B[2]), sig, nullptr, h);
+                        fast_update<R, AXZ>(s0, s1, s2, htx, hty, htz, h1x, h1y, h1z, sp, R(a.axis[0]), R(a.axis[1]),
+                                            R(a.axis[2]), R(a.B[0]), R(a.B[1]), R(a.B[2]), sig, nullptr, h);
                     }
                     sx[at] = s0;
                     sy[at] = s1;
@@ -419,20 +947,10 @@ __global__ void resident_kernel(ResArgs<R> a, int64_t nsteps)
             }
             // one-cell TTM, t_n -> t_n+1 (no diffusion on a single cell)
             if (threadIdx.x == 0 && a.ttm_active) {
-                const double delta = a.dt / D.substeps;
-                for (int k = 0; k < D.substeps; ++k) {
-                    const double tt = double(step) * a.dt + double(k) * delta;
-                    double src = 0.0;
-                    if (a.tp.source != TTS_SOURCE_NONE) {
-                        const double zz = (tt - D.t0) / D.sigma_t;
-                        src = D.P0 * exp(-0.5 * zz * zz);
-                    }
-                    const double xch = a.tp.G * (Te - Tl);
-                    const double dE = delta * (-xch + src);
-                    deposited += delta * src * D.cell_volume;
-                    Tl += delta * xch / a.tp.C_l;
-                    Te = sqrt(2.0 * (0.5 * a.tp.gamma_e * Te * Te + dE) / a.tp.gamma_e);
-                }
+                double T[2] = {Te, Tl};
+                resident_bath<R>(a, D, step, 1, T, &deposited, nullptr);
+                Te = T[0];
+                Tl = T[1];
             }
             if (a.sample_every > 0 && (step + 1) % a.sample_every == 0) {
                 if (threadIdx.x == 0) {
@@ -480,11 +998,26 @@ struct EngineState {
     CheckerInst *ci = nullptr;
     int64_t work = 0;
     int K = 2;
+    uint32_t shape[3] = {0, 0, 0};   // cells of every instance
+    uint32_t inst_base = 0;
+    int bx = 64, by = 4;             // pass block shape
+    bool axis_z = false;             // anisotropy axis is +z
+    bool pair = false;               // FP32 checker on site pairs
+    bool noise = false;              // some species has alpha > 0
+    TileArgs tile{};                 // pair engine staged in shared memory (bx = by = 0)
+    int cell_formula = 0;            // the pair kernels compute the TTM cell of a site
+    int cell0 = 0, cstride = 0;
+    uint32_t ncell[3] = {1, 1, 1};
+    size_t tile_smem = 0;
+    int tile_grid = 0;
+    std::vector<std::pair<int, int>> configs;   // checker: (bx, by); resident: (threads, 0)
+    int config = 0;
     // resident
     ResInst *ri = nullptr;
     int *order = nullptr;
     int *queue = nullptr;
     int nmax = 0;
+    int sm_count = 0;
     int block = 256;
     size_t smem = 0;
     int grid = 0;
@@ -551,7 +1084,67 @@ void fill_species(const tts_system_desc &d, FastSpecies<R> *out)
     }
 }
 
+f2 host_f2(double a, double b)
+{
+    const float fa = static_cast<float>(a), fb = static_cast<float>(b);
+    uint32_t ua, ub;
+    std::memcpy(&ua, &fa, 4);
+    std::memcpy(&ub, &fb, 4);
+    return f2{static_cast<unsigned long long>(ua) | (static_cast<unsigned long long>(ub) << 32)};
+}
+f2 host_splat(double a) { return host_f2(a, a); }
+
+// Constants of one pass of the pair kernel (h = dt / 2 or dt).
+PairConsts make_pair_consts(const EngineState *e, const StepParams &p, int hsel)
+{
+    const double h = hsel ? p.dt : 0.5 * p.dt;
+    const FastSpecies<double> *sp = e->spd;
+    auto cd = [](double v0, double v1, f2 &c, f2 &d) {
+        c = host_splat(v0);
+        d = host_splat(v1 - v0);
+    };
+    PairConsts k{};
+    cd(sp[0].J0, sp[1].J0, k.J0c, k.J0d);
+    cd(sp[0].J1 - sp[0].J0, sp[1].J1 - sp[1].J0, k.dJc, k.dJd);
+    cd(sp[0].kappa, sp[1].kappa, k.kc, k.kd);
+    cd(sp[0].alpha, sp[1].alpha, k.alc, k.ald);
+    cd(-0.5 * sp[0].kappa * sp[0].gprime * h, -0.5 * sp[1].kappa * sp[1].gprime * h, k.khgc, k.khgd);
+    cd(sp[0].gprime * h, sp[1].gprime * h, k.ghc, k.ghd);
+    const double log2e = 1.0 / std::log(2.0);
+    cd(-sp[0].alpha * log2e, -sp[1].alpha * log2e, k.nalc, k.nald);
+    k.nx = host_splat(p.axis[0]);
+    k.ny = host_splat(p.axis[1]);
+    k.nz = host_splat(p.axis[2]);
+    k.Bx = host_splat(p.B[0]);
+    k.By = host_splat(p.B[1]);
+    k.Bz = host_splat(p.B[2]);
+    k.one = host_splat(1.0);
+    k.neg1 = host_splat(-1.0);
+    k.u_scale = host_splat(std::ldexp(1.0, -23));
+    k.u_off = host_splat(std::ldexp(1.0, -24));
+    k.m2ln2 = host_splat(-2.0 * std::log(2.0));
+    k.twopi = host_splat(2.0 * M_PI);
+    k.negpi = host_splat(-M_PI);
+    k.s3 = host_splat(-1.0 / 6.0);
+    k.s5 = host_splat(1.0 / 120.0);
+    k.s7 = host_splat(-1.0 / 5040.0);
+    k.c2 = host_splat(-0.5);
+    k.c4 = host_splat(1.0 / 24.0);
+    k.c6 = host_splat(-1.0 / 720.0);
+    k.c8 = host_splat(1.0 / 40320.0);
+    return k;
+}
+
 size_t resident_bytes(int n, int precision) { return size_t(n) * (3 * (precision == 64 ? 8 : 4) + 1) + 16; }
+
+const void *resident_fn(int precision, bool axis_z)
+{
+    if (precision == 64)
+        return axis_z ? reinterpret_cast<const void *>(resident_kernel<double, true>)
+                      : reinterpret_cast<const void *>(resident_kernel<double, false>);
+    return axis_z ? reinterpret_cast<const void *>(resident_kernel<float, true>)
+                  : reinterpret_cast<const void *>(resident_kernel<float, false>);
+}
 
 bool fastdiv_ok(uint32_t d, uint32_t limit)
 {
@@ -582,6 +1175,8 @@ int engine_select(const tts_system_desc &d, const std::vector<HostInstance> &hos
     for (const HostInstance &hi : host)
         for (int k = 0; k < 3; ++k)
             even_equal = even_equal && hi.cells[k] % 2 == 0 && hi.cells[k] == host[0].cells[k];
+    // grid (x blocks, Lz, instances): y and z are limited to 65535
+    even_equal = even_equal && host[0].cells[2] <= 65535 && host.size() <= 65535;
     if (requested == TTS_ENGINE_RESIDENT) return fits ? TTS_ENGINE_RESIDENT : -1;
     if (requested == TTS_ENGINE_CHECKER) return even_equal ? TTS_ENGINE_CHECKER : -1;
     // AUTO: many small instances -> resident; otherwise large even lattices -> checker
@@ -590,6 +1185,89 @@ int engine_select(const tts_system_desc &d, const std::vector<HostInstance> &hos
     if (fits) return TTS_ENGINE_RESIDENT;
     return -1;
 }
+
+namespace {
+// Does cell0 + i cstride + (cz ncy + cy) ncx + cx, c_k = floor(k n_k / L_k),
+// reproduce the cell map of every checker slot?  Sets the engine's formula.
+void check_cell_formula(EngineState *e, const std::vector<DevInstance> &dinst, const std::vector<int> &cellmap)
+{
+    e->cell_formula = 0;
+    if (!e->pair || dinst.empty() || int64_t(cellmap.size()) != e->n_total) return;
+    const DevInstance &d0 = dinst[0];
+    const int cstride = dinst.size() > 1 ? dinst[1].cell_begin - d0.cell_begin : d0.ncells;
+    uint32_t nc[3];
+    for (int k = 0; k < 3; ++k) nc[k] = static_cast<uint32_t>(std::max(1, d0.cells[k]));
+    if (int64_t(nc[0]) * nc[1] * nc[2] != d0.ncells && !(d0.ncells == 1)) return;
+    if (d0.ncells == 1) nc[0] = nc[1] = nc[2] = 1;
+    for (size_t i = 0; i < dinst.size(); ++i)
+        if (dinst[i].cell_begin != d0.cell_begin + int(i) * cstride || dinst[i].ncells != d0.ncells ||
+            dinst[i].slot_begin != int64_t(i) * (e->n_total / e->n_inst))
+            return;
+    const uint32_t Lx = e->shape[0], Ly = e->shape[1], Lz = e->shape[2], hx = Lx / 2;
+    const uint32_t L[3] = {Lx, Ly, Lz};
+    for (int k = 0; k < 3; ++k)
+        if (!fastdiv_ok(L[k], L[k] * nc[k])) return;
+    const int64_t per = e->n_total / e->n_inst, nhalf = per / 2;
+    for (size_t i = 0; i < dinst.size(); ++i)
+        for (int64_t s = 0; s < per; ++s) {
+            const int64_t colour = s / nhalf, r = s - colour * nhalf;
+            const uint32_t z = static_cast<uint32_t>(r / (int64_t(Ly) * hx));
+            const uint32_t y = static_cast<uint32_t>((r / hx) % Ly), kx = static_cast<uint32_t>(r % hx);
+            const uint32_t x = 2 * kx + ((y + z + uint32_t(colour)) & 1u);
+            const uint32_t cx = x * nc[0] / Lx, cy = y * nc[1] / Ly, cz = z * nc[2] / Lz;
+            const int want = d0.cell_begin + int(i) * cstride + int((cz * nc[1] + cy) * nc[0] + cx);
+            if (cellmap[size_t(int64_t(i) * per + s)] != want) return;
+        }
+    e->cell0 = d0.cell_begin;
+    e->cstride = cstride;
+    for (int k = 0; k < 3; ++k) e->ncell[k] = nc[k];
+    e->cell_formula = 1;
+}
+
+// Shape check and launch set-up of the shared-memory staged pair pass: hx a
+// power of two in [8, 256], tile rows by = the largest divisor of Ly/2 with
+// by hx <= 256, one wave of CTAs over the (column, z) planes.
+bool setup_tiled(EngineState *e)
+{
+    const uint32_t hx = e->shape[0] / 2, Ly2 = e->shape[1] / 2, Lz = e->shape[2];
+    if (hx < 8 || hx > 256 || (hx & (hx - 1)) != 0 || Ly2 < 1) return false;
+    uint32_t by = 0;
+    for (uint32_t c = std::min<uint32_t>(256 / hx, Ly2); c >= 1; --c)
+        if (Ly2 % c == 0) {
+            by = c;
+            break;
+        }
+    if (by == 0) return false;
+    TileArgs t{};
+    t.by = by;
+    t.hx_shift = 0;
+    while ((1u << t.hx_shift) < hx) ++t.hx_shift;
+    t.nyb = Ly2 / by;
+    t.ncol = static_cast<uint32_t>(e->n_inst) * t.nyb;
+    t.units = uint64_t(t.ncol) * Lz;
+    const size_t to = size_t(by + 2) * hx, tw = size_t(by) * hx;
+    const size_t smem = (8 * to + 4 * tw) * 16 + 6 * sizeof(uint64_t);
+    int dev = 0, nsm = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    for (const void *fn : {reinterpret_cast<const void *>(checker_pair_tiled_kernel<true>),
+                           reinterpret_cast<const void *>(checker_pair_tiled_kernel<false>)}) {
+        int ps = 0;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, fn, 256, smem) != cudaSuccess || ps < 1) {
+            cudaGetLastError();
+            return false;
+        }
+        per_sm = per_sm == 0 ? ps : std::min(per_sm, ps);
+    }
+    e->tile = t;
+    e->tile_smem = smem;
+    e->tile_grid = static_cast<int>(std::min<uint64_t>(t.units, uint64_t(nsm) * per_sm));
+    return true;
+}
+}  // namespace
 
 int engine_create(const tts_system_desc &d, const std::vector<HostInstance> &host,
                   const std::vector<std::vector<int64_t>> &slot_of_atom, const std::vector<DevInstance> &dinst,
@@ -606,6 +1284,11 @@ int engine_create(const tts_system_desc &d, const std::vector<HostInstance> &hos
     for (const DevInstance &di : dinst) e->n_total += di.n;
     fill_species<float>(d, e->spf);
     fill_species<double>(d, e->spd);
+    for (int t = 0; t < d.nspecies; ++t) e->noise = e->noise || d.alpha[t] > 0.0;
+    {
+        const double an = std::sqrt(d.axis[0] * d.axis[0] + d.axis[1] * d.axis[1] + d.axis[2] * d.axis[2]);
+        e->axis_z = an > 0.0 && d.axis[0] == 0.0 && d.axis[1] == 0.0 && d.axis[2] > 0.0;
+    }
     cudaError_t ce;
     if (engine == TTS_ENGINE_CHECKER) {
         std::vector<CheckerInst> ci(e->n_inst);
@@ -635,6 +1318,43 @@ int engine_create(const tts_system_desc &d, const std::vector<HostInstance> &hos
             prefix += c.nhalf;
         }
         e->work = prefix;
+        for (int k = 0; k < 3; ++k) e->shape[k] = static_cast<uint32_t>(host[0].cells[k]);
+        e->inst_base = static_cast<uint32_t>(d.instance_base);
+        e->pair = d.precision == 32;
+        // x rows of hx = Lx/2 colour sites in warps, the rest of the threads in y
+        const int hxs = static_cast<int>(e->shape[0] / 2);
+        if (e->pair) {
+            // (bx, by) pairs x pair rows; (0, 0): the shared-memory staged
+            // pass.  Default: 128 threads.
+            e->bx = hxs >= 64 ? 64 : 32;
+            e->by = 128 / e->bx;
+            for (int bx : {32, 64, 128})
+                if (bx <= std::max(32, hxs))
+                    for (int threads : {128, 256}) e->configs.push_back({bx, threads / bx});
+        } else {
+            e->bx = hxs >= 128 ? 128 : (hxs >= 64 ? 64 : 32);
+            e->by = 256 / e->bx;
+            for (int bx : {32, 64, 128})
+                if (bx <= std::max(32, hxs))
+                    for (int threads : {128, 256})
+                        if (threads / bx >= 1) e->configs.push_back({bx, threads / bx});
+        }
+        // the default first
+        for (size_t k = 0; k < e->configs.size(); ++k)
+            if (e->configs[k].first == e->bx && e->configs[k].second == e->by) {
+                std::swap(e->configs[0], e->configs[k]);
+                break;
+            }
+        e->config = 0;
+        if (e->pair) {
+            std::vector<int> cm(static_cast<size_t>(e->n_total));
+            if (cudaStreamSynchronize(st) == cudaSuccess &&
+                cudaMemcpy(cm.data(), b.cell, cm.size() * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess)
+                check_cell_formula(e, dinst, cm);
+            else
+                cudaGetLastError();
+            if (setup_tiled(e)) e->configs.push_back({0, 0});
+        }
         const size_t vs = d.precision == 64 ? sizeof(double4a) : sizeof(float4);
         if ((ce = cudaMalloc(&e->S, size_t(e->n_total) * vs)) != cudaSuccess ||
             (ce = cudaMalloc(reinterpret_cast<void **>(&e->ci), ci.size() * sizeof(CheckerInst))) != cudaSuccess) {
@@ -678,23 +1398,24 @@ int engine_create(const tts_system_desc &d, const std::vector<HostInstance> &hos
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         e->block = 512;
-        cudaError_t a1 = d.precision == 64
-                             ? cudaFuncSetAttribute(resident_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    static_cast<int>(e->smem))
-                             : cudaFuncSetAttribute(resident_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    static_cast<int>(e->smem));
+        const void *fn = resident_fn(d.precision, e->axis_z);
+        cudaError_t a1 = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(e->smem));
         int per_sm = 0;
-        if (a1 == cudaSuccess)
-            a1 = d.precision == 64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_kernel<double>,
-                                                                                  e->block, e->smem)
-                                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_kernel<float>,
-                                                                                  e->block, e->smem);
+        if (a1 == cudaSuccess) a1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, e->block, e->smem);
         if (a1 != cudaSuccess || per_sm < 1) {
             cudaGetLastError();
             delete e;
             return eng_fail(TTS_ERR_UNSUPPORTED, "resident kernel does not fit one CTA per SM");
         }
         e->grid = std::min(e->n_inst, nsm * per_sm);
+        e->configs.push_back({512, 0});
+        for (int threads : {256, 384}) {
+            int ps = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, fn, threads, e->smem) == cudaSuccess && ps >= 1)
+                e->configs.push_back({threads, 0});
+            cudaGetLastError();
+        }
+        e->sm_count = nsm;
         if ((ce = cudaMalloc(reinterpret_cast<void **>(&e->ri), ri.size() * sizeof(ResInst))) != cudaSuccess ||
             (ce = cudaMalloc(reinterpret_cast<void **>(&e->order), order.size() * sizeof(int))) != cudaSuccess ||
             (ce = cudaMalloc(reinterpret_cast<void **>(&e->queue), sizeof(int))) != cudaSuccess) {
@@ -728,24 +1449,126 @@ void engine_destroy(EngineState *e)
 
 bool engine_multi_step(const EngineState *e) { return e && e->engine == TTS_ENGINE_RESIDENT; }
 
+int engine_num_configs(const EngineState *e) { return e ? static_cast<int>(e->configs.size()) : 0; }
+int engine_config(const EngineState *e) { return e ? e->config : 0; }
+
+void engine_set_config(EngineState *e, int index)
+{
+    if (!e || index < 0 || index >= static_cast<int>(e->configs.size())) return;
+    e->config = index;
+    if (e->engine == TTS_ENGINE_CHECKER) {
+        e->bx = e->configs[index].first;
+        e->by = e->configs[index].second;
+    } else if (e->engine == TTS_ENGINE_RESIDENT) {
+        e->block = e->configs[index].first;
+        int ps = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, resident_fn(e->precision, e->axis_z), e->block, e->smem) !=
+                cudaSuccess ||
+            ps < 1) {
+            cudaGetLastError();
+            ps = 1;
+        }
+        e->grid = std::min(e->n_inst, e->sm_count * ps);
+    }
+}
+
+namespace {
+// Launch arguments of the FP32 pair kernels for a pass with step h(hsel).
+PairArgs pair_args(const EngineState *e, const StepParams &p, const DevBuffers &b, int hsel)
+{
+    PairArgs a{};
+    a.S = static_cast<ulonglong2 *>(e->S);
+    a.cell = b.cell;
+    a.sigma = static_cast<const float *>(b.sigma);
+    a.step = b.step;
+    a.health = b.health;
+    a.k = make_pair_consts(e, p, hsel);
+    a.key0 = p.key0;
+    a.key1 = p.key1;
+    a.Lx = e->shape[0];
+    a.Ly = e->shape[1];
+    a.Lz = e->shape[2];
+    a.hx = e->shape[0] / 2;
+    a.Ly2 = e->shape[1] / 2;
+    a.nkx = e->bx ? (a.hx + e->bx - 1) / e->bx : 0;
+    a.nhalf = static_cast<uint32_t>(e->n_total / e->n_inst / 2);
+    a.npair = a.nhalf / 2;
+    a.n_inst_sites = e->n_total / e->n_inst;
+    a.inst_base = e->inst_base;
+    a.noise = e->noise ? 1 : 0;
+    a.cell_formula = e->cell_formula;
+    a.cell0 = e->cell0;
+    a.cstride = e->cstride;
+    a.ncx = e->ncell[0];
+    a.ncy = e->ncell[1];
+    a.ncz = e->ncell[2];
+    a.dLx = make_fastdiv(e->shape[0]);
+    a.dLy = make_fastdiv(e->shape[1]);
+    a.dLz = make_fastdiv(e->shape[2]);
+    return a;
+}
+
+void launch_pair_to_general(EngineState *e, const DevBuffers &b, cudaStream_t st, int sample_every, int conditional)
+{
+    const int bs = 256;
+    const int64_t np = e->n_total / 2;
+    pair_to_general_kernel<<<(np + bs - 1) / bs, bs, 0, st>>>(
+        static_cast<const float4 *>(e->S), static_cast<float *>(b.sx), static_cast<float *>(b.sy),
+        static_cast<float *>(b.sz), np, e->shape[0] / 2, e->shape[1] / 2,
+        static_cast<uint32_t>(e->n_total / e->n_inst / 4), b.step, sample_every, conditional);
+}
+}  // namespace
+
+cudaError_t engine_obs_partials(EngineState *e, const StepParams &p, const DevBuffers &b, int mode, cudaStream_t st)
+{
+    if (!e || e->engine != TTS_ENGINE_CHECKER || !e->pair) return cudaErrorNotSupported;
+    PairObsArgs o{};
+    o.obs_block_inst = b.obs_block_inst;
+    o.inst = b.inst;
+    o.obs_partial = b.obs_partial;
+    o.obs_blocks = p.obs_blocks;
+    o.sample_every = p.sample_every;
+    for (int t = 0; t < TTS_MAX_SPECIES; ++t) {
+        o.mu[t] = p.sp[t].mu;
+        o.K[t] = p.sp[t].K;
+    }
+    const int grid = p.obs_blocks < 1184 ? p.obs_blocks : 1184;
+    checker_pair_obs_kernel<<<grid, kObsBlock, 0, st>>>(pair_args(e, p, b, 0), o, mode);
+    return cudaGetLastError();
+}
+
 cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuffers &b, const TtmParams &tp,
                                bool ttm_active, cudaStream_t st, int *kernels, cudaEvent_t ev0, cudaEvent_t ev1)
 {
     *kernels = 0;
     if (e->engine != TTS_ENGINE_CHECKER) return cudaErrorNotSupported;
-    cudaError_t err = launch_sigma(p, b, p.ncells_total, e->precision, st);
-    ++*kernels;
+    cudaError_t err = cudaSuccess;
+    if (p.sigma_per_step) {
+        err = launch_sigma(p, b, p.ncells_total, e->precision, st);
+        ++*kernels;
+    }
     if (err == cudaSuccess && ev0) err = cudaEventRecord(ev0, st);
     const int npass = 2 * e->K - 1;
     for (int pass = 0; pass < npass && err == cudaSuccess; ++pass) {
         const int c = pass < e->K - 1 ? pass : (pass == e->K - 1 ? e->K - 1 : 2 * e->K - 2 - pass);
         const int hsel = pass == e->K - 1 ? 1 : 0;
-        const int bs = 256;
-        const int64_t gs = (e->work + bs - 1) / bs;
+        const dim3 block(e->bx, e->by);
+        const uint32_t nkx = e->bx ? (e->shape[0] / 2 + e->bx - 1) / e->bx : 0;
+        const dim3 grid(e->by ? nkx * ((e->shape[1] + e->by - 1) / e->by) : 0, e->shape[2], e->n_inst);
+        auto fill_shape = [&](auto &a) {
+            a.nkx = nkx;
+            a.Lx = e->shape[0];
+            a.Ly = e->shape[1];
+            a.Lz = e->shape[2];
+            a.hx = e->shape[0] / 2;
+            a.nhalf = static_cast<uint32_t>(e->n_total / e->n_inst / 2);
+            a.n_inst_sites = e->n_total / e->n_inst;
+            a.inst_base = e->inst_base;
+        };
         if (e->precision == 64) {
             CheckerArgs<double> a{};
             a.S = static_cast<double4a *>(e->S);
-            a.ci = e->ci;
+            fill_shape(a);
             a.cell = b.cell;
             a.sigma = static_cast<const double *>(b.sigma);
             a.step = b.step;
@@ -754,53 +1577,50 @@ cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuf
             a.nx = p.axis[0]; a.ny = p.axis[1]; a.nz = p.axis[2];
             a.Bx = p.B[0]; a.By = p.B[1]; a.Bz = p.B[2];
             a.dt = p.dt;
-            a.key0 = p.key0; a.key1 = p.key1;
-            a.n_inst = e->n_inst;
-            a.total = e->work;
-            checker_pass_kernel<double><<<gs, bs, 0, st>>>(a, c, hsel, pass);
+            a.key0 = p.key0;
+            a.key1 = p.key1;
+            if (e->axis_z)
+                checker_pass_kernel<double, true><<<grid, block, 0, st>>>(a, c, hsel, pass);
+            else
+                checker_pass_kernel<double, false><<<grid, block, 0, st>>>(a, c, hsel, pass);
         } else {
-            CheckerArgs<float> a{};
-            a.S = static_cast<float4 *>(e->S);
-            a.ci = e->ci;
-            a.cell = b.cell;
-            a.sigma = static_cast<const float *>(b.sigma);
-            a.step = b.step;
-            a.health = b.health;
-            for (int t = 0; t < TTS_MAX_SPECIES; ++t) a.sp[t] = e->spf[t];
-            a.nx = float(p.axis[0]); a.ny = float(p.axis[1]); a.nz = float(p.axis[2]);
-            a.Bx = float(p.B[0]); a.By = float(p.B[1]); a.Bz = float(p.B[2]);
-            a.dt = float(p.dt);
-            a.key0 = p.key0; a.key1 = p.key1;
-            a.n_inst = e->n_inst;
-            a.total = e->work;
-            checker_pass_kernel<float><<<gs, bs, 0, st>>>(a, c, hsel, pass);
+            const PairArgs a = pair_args(e, p, b, hsel);
+            if (e->bx == 0) {
+                if (e->axis_z)
+                    checker_pair_tiled_kernel<true><<<e->tile_grid, 256, e->tile_smem, st>>>(a, e->tile, c, hsel, pass);
+                else
+                    checker_pair_tiled_kernel<false><<<e->tile_grid, 256, e->tile_smem, st>>>(a, e->tile, c, hsel, pass);
+            } else {
+                const dim3 pgrid(a.nkx * ((a.Ly2 + e->by - 1) / e->by), e->shape[2], e->n_inst);
+                if (e->axis_z)
+                    checker_pair_kernel<true><<<pgrid, block, 0, st>>>(a, c, hsel, pass);
+                else
+                    checker_pair_kernel<false><<<pgrid, block, 0, st>>>(a, c, hsel, pass);
+            }
         }
         err = cudaGetLastError();
         ++*kernels;
     }
     if (err == cudaSuccess && ev1) err = cudaEventRecord(ev1, st);
-    if (err == cudaSuccess && ttm_active) {
-        err = launch_ttm(p, b, tp, p.n_instances, st);
-        ++*kernels;
-    }
+    bool partials = false;
     if (err == cudaSuccess && p.sample_every > 0) {
-        const int bs = 256;
-        const int64_t gs = (e->n_total + bs - 1) / bs;
-        if (e->precision == 64)
-            to_general_kernel<double><<<gs, bs, 0, st>>>(static_cast<const double4a *>(e->S), static_cast<double *>(b.sx),
-                                                         static_cast<double *>(b.sy), static_cast<double *>(b.sz),
-                                                         e->n_total, b.step, p.sample_every, 1);
-        else
-            to_general_kernel<float><<<gs, bs, 0, st>>>(static_cast<const float4 *>(e->S), static_cast<float *>(b.sx),
-                                                        static_cast<float *>(b.sy), static_cast<float *>(b.sz),
-                                                        e->n_total, b.step, p.sample_every, 1);
-        err = cudaGetLastError();
+        if (e->pair) {
+            // observables straight from the pair layout (sampling steps only)
+            err = engine_obs_partials(e, p, b, 0, st);
+            partials = true;
+        } else {
+            const int bs = 256;
+            const int64_t gs = (e->n_total + bs - 1) / bs;
+            to_general_kernel<double><<<gs, bs, 0, st>>>(static_cast<const double4a *>(e->S),
+                                                         static_cast<double *>(b.sx), static_cast<double *>(b.sy),
+                                                         static_cast<double *>(b.sz), e->n_total, b.step,
+                                                         p.sample_every, 1);
+            err = cudaGetLastError();
+        }
         ++*kernels;
     }
-    if (err == cudaSuccess) {
-        err = launch_obs(p, b, e->precision, p.obs_blocks, 0, st);
-        *kernels += 2;
-    }
+    if (err == cudaSuccess)
+        err = step_tail(p, b, tp, ttm_active, p.n_instances, e->precision, p.obs_blocks, st, kernels, partials);
     return err;
 }
 
@@ -850,7 +1670,10 @@ cudaError_t engine_run_steps(EngineState *e, const StepParams &p, const DevBuffe
             a.sz = static_cast<double *>(b.sz);
             fill(a);
             for (int t = 0; t < TTS_MAX_SPECIES; ++t) a.sp[t] = e->spd[t];
-            resident_kernel<double><<<e->grid, e->block, e->smem, st>>>(a, nsteps);
+            if (e->axis_z)
+                resident_kernel<double, true><<<e->grid, e->block, e->smem, st>>>(a, nsteps);
+            else
+                resident_kernel<double, false><<<e->grid, e->block, e->smem, st>>>(a, nsteps);
         } else {
             ResArgs<float> a{};
             a.sx = static_cast<float *>(b.sx);
@@ -858,7 +1681,10 @@ cudaError_t engine_run_steps(EngineState *e, const StepParams &p, const DevBuffe
             a.sz = static_cast<float *>(b.sz);
             fill(a);
             for (int t = 0; t < TTS_MAX_SPECIES; ++t) a.sp[t] = e->spf[t];
-            resident_kernel<float><<<e->grid, e->block, e->smem, st>>>(a, nsteps);
+            if (e->axis_z)
+                resident_kernel<float, true><<<e->grid, e->block, e->smem, st>>>(a, nsteps);
+            else
+                resident_kernel<float, false><<<e->grid, e->block, e->smem, st>>>(a, nsteps);
         }
         err = cudaGetLastError();
         ++*kernels;
@@ -872,9 +1698,11 @@ cudaError_t engine_run_steps(EngineState *e, const StepParams &p, const DevBuffe
     return err;
 }
 
-int engine_set_cells(EngineState *e, const std::vector<DevInstance> &dinst, const std::vector<int> &, cudaStream_t)
+int engine_set_cells(EngineState *e, const std::vector<DevInstance> &dinst, const std::vector<int> &cellmap,
+                     cudaStream_t)
 {
     e->dinst = dinst;
+    if (e->engine == TTS_ENGINE_CHECKER) check_cell_formula(e, dinst, cellmap);
     if (e->engine == TTS_ENGINE_RESIDENT)
         for (const DevInstance &di : dinst)
             if (di.ncells != 1) return eng_fail(TTS_ERR_UNSUPPORTED, "the resident engine takes one TTM cell per instance");
@@ -891,9 +1719,7 @@ cudaError_t engine_sync_to_general(EngineState *e, const DevBuffers &b, cudaStre
                                                      static_cast<double *>(b.sy), static_cast<double *>(b.sz),
                                                      e->n_total, b.step, 0, 0);
     else
-        to_general_kernel<float><<<gs, bs, 0, st>>>(static_cast<const float4 *>(e->S), static_cast<float *>(b.sx),
-                                                    static_cast<float *>(b.sy), static_cast<float *>(b.sz), e->n_total,
-                                                    b.step, 0, 0);
+        launch_pair_to_general(e, b, st, 0, 0);
     return cudaGetLastError();
 }
 
@@ -906,10 +1732,13 @@ cudaError_t engine_sync_from_general(EngineState *e, const DevBuffers &b, cudaSt
         from_general_kernel<double><<<gs, bs, 0, st>>>(static_cast<double4a *>(e->S), static_cast<const double *>(b.sx),
                                                        static_cast<const double *>(b.sy),
                                                        static_cast<const double *>(b.sz), b.species, e->n_total);
-    else
-        from_general_kernel<float><<<gs, bs, 0, st>>>(static_cast<float4 *>(e->S), static_cast<const float *>(b.sx),
-                                                      static_cast<const float *>(b.sy), static_cast<const float *>(b.sz),
-                                                      b.species, e->n_total);
+    else {
+        const int64_t np = e->n_total / 2;
+        pair_from_general_kernel<<<(np + bs - 1) / bs, bs, 0, st>>>(
+            static_cast<float4 *>(e->S), static_cast<const float *>(b.sx), static_cast<const float *>(b.sy),
+            static_cast<const float *>(b.sz), b.species, np, e->shape[0] / 2, e->shape[1] / 2,
+            static_cast<uint32_t>(e->n_total / e->n_inst / 4));
+    }
     return cudaGetLastError();
 }
 

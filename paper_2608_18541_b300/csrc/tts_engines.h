@@ -41,7 +41,16 @@ cudaError_t engine_run_steps(EngineState *e, const StepParams &p, const DevBuffe
 // A TTM grid was attached (the cell map of every slot is in DevBuffers::cell).
 int engine_set_cells(EngineState *e, const std::vector<DevInstance> &dinst, const std::vector<int> &cellmap,
                      cudaStream_t st);
+// Launch configurations the engine offers to the autotuner.
+int engine_num_configs(const EngineState *e);
+void engine_set_config(EngineState *e, int index);
+int engine_config(const EngineState *e);
+
 cudaError_t engine_sync_to_general(EngineState *e, const DevBuffers &b, cudaStream_t st);
+// Observable partial sums (the general kernel's per-block layout) straight
+// from the engine's own spin layout; cudaErrorNotSupported when the engine
+// has none.  mode 0: only on sampling steps; 1: now.
+cudaError_t engine_obs_partials(EngineState *e, const StepParams &p, const DevBuffers &b, int mode, cudaStream_t st);
 cudaError_t engine_sync_from_general(EngineState *e, const DevBuffers &b, cudaStream_t st);
 
 }  // namespace tts

@@ -89,18 +89,25 @@ struct FastSpecies {
 // neighbour spins, h1 = sum over species-1 neighbours), anisotropy, Zeeman,
 // noise sig * g, the midpoint anisotropy correction, the exact flow and
 // renormalisation.  Returns the new spin in (sx, sy, sz).
-template <typename R>
+// AXZ: the anisotropy axis is +z (n = (0, 0, 1)), which removes the
+// general projections.
+template <typename R, bool AXZ = false>
 __device__ __forceinline__ void fast_update(R &sx, R &sy, R &sz, R htx, R hty, R htz, R h1x, R h1y, R h1z,
                                             const FastSpecies<R> &sp, R nx, R ny, R nz, R Bex, R Bey, R Bez,
                                             R sig, const u32x4 *noise, R h)
 {
     using F = Fast<R>;
+    if (AXZ) {
+        nx = R(0);
+        ny = R(0);
+        nz = R(1);
+    }
     const R dJ = sp.J1 - sp.J0;
-    const R cn0 = sx * nx + sy * ny + sz * nz;
+    const R cn0 = AXZ ? sz : sx * nx + sy * ny + sz * nz;
     const R ka = sp.kappa * cn0;
-    R Bx = sp.J0 * htx + dJ * h1x + ka * nx + Bex;
-    R By = sp.J0 * hty + dJ * h1y + ka * ny + Bey;
-    R Bz = sp.J0 * htz + dJ * h1z + ka * nz + Bez;
+    R Bx = AXZ ? sp.J0 * htx + dJ * h1x + Bex : sp.J0 * htx + dJ * h1x + ka * nx + Bex;
+    R By = AXZ ? sp.J0 * hty + dJ * h1y + Bey : sp.J0 * hty + dJ * h1y + ka * ny + Bey;
+    R Bz = AXZ ? sp.J0 * htz + dJ * h1z + ka + Bez : sp.J0 * htz + dJ * h1z + ka * nz + Bez;
     if (noise) {
         R g1, g2, g3;
         F::gauss3(*noise, g1, g2, g3);
@@ -109,7 +116,11 @@ __device__ __forceinline__ void fast_update(R &sx, R &sy, R &sz, R htx, R hty, R
         Bz += sig * g3;
     }
     // on-site anisotropy taken at the predicted sub-step midpoint
-    if (sp.kappa != R(0)) {
+    if (AXZ) {
+        const R n_sxB = sx * By - sy * Bx;
+        const R sB = sx * Bx + sy * By + sz * Bz;
+        Bz += sp.kappa * R(0.5) * h * (-sp.gprime * (n_sxB + sp.alpha * (cn0 * sB - Bz)));
+    } else if (sp.kappa != R(0)) {
         const R cx = sy * Bz - sz * By, cy = sz * Bx - sx * Bz, cz = sx * By - sy * Bx;
         const R n_sxB = nx * cx + ny * cy + nz * cz;
         const R sB = sx * Bx + sy * By + sz * Bz;

@@ -99,12 +99,13 @@ __device__ __forceinline__ void exact_flow(R &sx, R &sy, R &sz, R Bx, R By, R Bz
 }
 
 // ---------------------------------------------------------------------------
+// Noise amplitude sqrt(2 alpha k_B T / (gamma mu h)) of one cell, written for
+// both species and both sub-step lengths (h = dt/2, dt).  One formula for
+// every kernel that refreshes the table, so a restart reproduces a
+// continuous run bit for bit.
 template <typename R>
-__global__ void sigma_kernel(StepParams p, const double *__restrict__ Te, R *__restrict__ sigma, int ncells)
+__device__ __forceinline__ void write_sigma(const StepParams &p, double T, R *__restrict__ sigma, int64_t g)
 {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ncells) return;
-    const double T = Te[g];
     for (int t = 0; t < TTS_MAX_SPECIES; ++t)
         for (int hs = 0; hs < 2; ++hs) {
             double v = 0.0;
@@ -114,6 +115,14 @@ __global__ void sigma_kernel(StepParams p, const double *__restrict__ Te, R *__r
             }
             sigma[(g * TTS_MAX_SPECIES + t) * 2 + hs] = static_cast<R>(v);
         }
+}
+
+template <typename R>
+__global__ void sigma_kernel(StepParams p, const double *__restrict__ Te, R *__restrict__ sigma, int ncells)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ncells) return;
+    write_sigma<R>(p, Te[g], sigma, g);
 }
 
 // Field of one slot from the neighbour table (J/mu already folded in), the
@@ -142,7 +151,7 @@ __device__ __forceinline__ void det_field(const StepParams &p, int64_t slot, int
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) pass_general_kernel(StepParams p, DevBuffers b, int pass,
+__global__ void __launch_bounds__(512) pass_general_kernel(StepParams p, DevBuffers b, int pass,
                                                            const PassRange *__restrict__ ranges, int nranges,
                                                            int64_t nwork)
 {
@@ -262,6 +271,57 @@ __global__ void ttm_kernel(StepParams p, DevBuffers b, TtmParams tp)
 }
 
 // ---------------------------------------------------------------------------
+// TTM with one sub-step per spin step (the usual case): the electron-energy
+// increments of all cells of all instances in one grid, then the update per
+// instance.
+// ---------------------------------------------------------------------------
+__global__ void ttm_increment_kernel(StepParams p, DevBuffers b, TtmParams tp, const int *__restrict__ cell_inst,
+                                     int ncells_total)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ncells_total) return;
+    const int inst = cell_inst[g];
+    const DevInstance &I = b.inst[inst];
+    const int c = g - I.cell_begin;
+    const double *Te = b.Te + I.cell_begin;
+    const int nxc = I.cells[0], nyc = I.cells[1], nzc = I.cells[2];
+    const int cx = c % nxc, cy = (c / nxc) % nyc, cz = c / (nxc * nyc);
+    const double Tc = Te[c];
+    double lap = 0.0;
+    if (nxc > 1)
+        lap += (Te[cz * nyc * nxc + cy * nxc + (cx + 1) % nxc] - 2.0 * Tc + Te[cz * nyc * nxc + cy * nxc + (cx + nxc - 1) % nxc]) /
+               (I.dx[0] * I.dx[0]);
+    if (nyc > 1)
+        lap += (Te[cz * nyc * nxc + ((cy + 1) % nyc) * nxc + cx] - 2.0 * Tc + Te[cz * nyc * nxc + ((cy + nyc - 1) % nyc) * nxc + cx]) /
+               (I.dx[1] * I.dx[1]);
+    if (nzc > 1)
+        lap += (Te[((cz + 1) % nzc) * nyc * nxc + cy * nxc + cx] - 2.0 * Tc +
+                Te[((cz + nzc - 1) % nzc) * nyc * nxc + cy * nxc + cx]) / (I.dx[2] * I.dx[2]);
+    double pulse = 0.0;
+    if (tp.source != TTS_SOURCE_NONE) {
+        const double z = (double(*b.step) * p.dt - I.t0) / I.sigma_t;
+        pulse = I.P0 * exp(-0.5 * z * z);
+    }
+    const double src = pulse * b.src_shape[g];
+    const double x = tp.G * (Tc - b.Tl[g]);
+    b.ttm_scratch[g] = p.dt * (tp.kappa_e * lap - x + src);
+    b.Tl[g] += p.dt * x / tp.C_l;
+}
+
+// New T_e of every cell and, from it, the noise table of the next step; the
+// step counter advances here when no observable kernel follows.
+template <typename R>
+__global__ void ttm_apply_kernel(StepParams p, DevBuffers b, TtmParams tp, int ncells_total, int inc_step)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (inc_step && g == 0) *b.step += 1;
+    if (g >= ncells_total) return;
+    const double T = sqrt(2.0 * (0.5 * tp.gamma_e * b.Te[g] * b.Te[g] + b.ttm_scratch[g]) / tp.gamma_e);
+    b.Te[g] = T;
+    write_sigma<R>(p, T, static_cast<R *>(b.sigma), g);
+}
+
+// ---------------------------------------------------------------------------
 // Observables.  mode 0: inside a step (sample when (step+1) % every == 0, into
 // the ring, then advance the step counter); mode 1: now, into obs_now.
 // ---------------------------------------------------------------------------
@@ -271,56 +331,54 @@ __global__ void __launch_bounds__(kObsBlock) obs_partial_kernel(StepParams p, De
     const int64_t step = *b.step;
     const int64_t clock = p.lattice_on ? *p.lstep : step;
     if (mode == 0 && (p.sample_every <= 0 || (clock + 1) % p.sample_every != 0)) return;
-    const int inst = b.obs_block_inst[blockIdx.x];
-    const DevInstance I = b.inst[inst];
-    const int64_t first = b.obs_block_begin[blockIdx.x];
-    const int64_t end = I.slot_begin + I.n;
-    double acc[kObsFields];
-#pragma unroll
-    for (int k = 0; k < kObsFields; ++k) acc[k] = 0.0;
     const R *S0 = static_cast<const R *>(b.sx), *S1 = static_cast<const R *>(b.sy), *S2 = static_cast<const R *>(b.sz);
-    const int64_t slot = first + threadIdx.x;
-    if (slot < end) {
-        const int t = b.species[slot];
-        const double sx = S0[slot], sy = S1[slot], sz = S2[slot];
-        // exchange part alone (for the pair energy), then the full field
-        double hx = 0, hy = 0, hz = 0;
-        const R *w = static_cast<const R *>(b.nbr_w);
-        for (int k = 0; k < p.zmax; ++k) {
-            const int64_t e = int64_t(k) * p.n_total + slot;
-            const double J = w[e];
-            const int j = b.nbr[e];
-            hx += J * double(S0[j]);
-            hy += J * double(S1[j]);
-            hz += J * double(S2[j]);
+    const R *w = static_cast<const R *>(b.nbr_w);
+    // a small persistent grid walks the observable blocks, so steps that do
+    // not sample cost one early exit per CTA
+    for (int blk = blockIdx.x; blk < p.obs_blocks; blk += gridDim.x) {
+        const int inst = b.obs_block_inst[blk];
+        const DevInstance I = b.inst[inst];
+        const int64_t first = b.obs_block_begin[blk];
+        const int64_t end = I.slot_begin + I.n;
+        double acc[kObsFields];
+#pragma unroll
+        for (int k = 0; k < kObsFields; ++k) acc[k] = 0.0;
+        for (int j = 0; j < kObsSpan / kObsBlock; ++j) {
+            const int64_t slot = first + threadIdx.x + int64_t(j) * kObsBlock;
+            if (slot >= end) break;
+            const int t = b.species[slot];
+            const double sx = S0[slot], sy = S1[slot], sz = S2[slot];
+            double hx = 0, hy = 0, hz = 0;
+            for (int k = 0; k < p.zmax; ++k) {
+                const int64_t e = int64_t(k) * p.n_total + slot;
+                const double J = w[e];
+                const int jn = b.nbr[e];
+                hx += J * double(S0[jn]);
+                hy += J * double(S1[jn]);
+                hz += J * double(S2[jn]);
+            }
+            const double mu = p.sp[t].mu;
+            const double sn = sx * p.axis[0] + sy * p.axis[1] + sz * p.axis[2];
+            const double ka = p.sp[t].kappa * sn;
+            const double Bx = hx + ka * p.axis[0] + p.B[0];
+            const double By = hy + ka * p.axis[1] + p.B[1];
+            const double Bz = hz + ka * p.axis[2] + p.B[2];
+            const double Hx = mu * Bx, Hy = mu * By, Hz = mu * Bz;
+            const double cx = sy * Hz - sz * Hy, cy = sz * Hx - sx * Hz, cz = sx * Hy - sy * Hx;
+            const double v[12] = {1.0, sx, sy, sz, 0.0, 0.0, 0.0,
+                                  -0.5 * mu * (sx * hx + sy * hy + sz * hz),
+                                  -p.sp[t].K * sn * sn,
+                                  -mu * (p.B[0] * sx + p.B[1] * sy + p.B[2] * sz),
+                                  cx * cx + cy * cy + cz * cz,
+                                  sx * Hx + sy * Hy + sz * Hz};
+            // species select without indexing the accumulator by t
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                acc[k] += t == 0 ? v[k] : 0.0;
+                acc[12 + k] += t == 0 ? 0.0 : v[k];
+            }
         }
-        const double mu = p.sp[t].mu;
-        const double sn = sx * p.axis[0] + sy * p.axis[1] + sz * p.axis[2];
-        const double ka = p.sp[t].kappa * sn;
-        const double Bx = hx + ka * p.axis[0] + p.B[0];
-        const double By = hy + ka * p.axis[1] + p.B[1];
-        const double Bz = hz + ka * p.axis[2] + p.B[2];
-        const double Hx = mu * Bx, Hy = mu * By, Hz = mu * Bz;
-        const double cx = sy * Hz - sz * Hy, cy = sz * Hx - sx * Hz, cz = sx * Hy - sy * Hx;
-        double *a = acc + 12 * t;
-        a[0] = 1.0;
-        a[1] = sx; a[2] = sy; a[3] = sz;
-        a[7] = -0.5 * mu * (sx * hx + sy * hy + sz * hz);
-        a[8] = -p.sp[t].K * sn * sn;
-        a[9] = -mu * (p.B[0] * sx + p.B[1] * sy + p.B[2] * sz);
-        a[10] = cx * cx + cy * cy + cz * cz;
-        a[11] = sx * Hx + sy * Hy + sz * Hz;
-    }
-    __shared__ double red[kObsBlock];
-    for (int k = 0; k < kObsFields; ++k) {
-        red[threadIdx.x] = acc[k];
-        __syncthreads();
-        for (int s = kObsBlock / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) b.obs_partial[int64_t(blockIdx.x) * kObsFields + k] = red[0];
-        __syncthreads();
+        block_sum_store<kObsFields>(acc, b.obs_partial + int64_t(blk) * kObsFields);
     }
 }
 
@@ -328,87 +386,100 @@ __global__ void __launch_bounds__(kObsBlock) obs_partial_kernel(StepParams p, De
 // 4..6 unused, 7 exchange energy (half of mu s.h per atom, each pair counted
 // twice), 8 anisotropy, 9 Zeeman, 10 sum |s x H|^2, 11 sum s.H.  The moment-
 // weighted direction is sum_t mu_t sum_{i in t} s_i / sum_t mu_t n_t.
-__global__ void obs_final_kernel(StepParams p, DevBuffers b, int mode)
+__global__ void obs_reduce_kernel(StepParams p, DevBuffers b, int mode)
 {
     const int64_t step = *b.step;
     const int64_t clock = p.lattice_on ? *p.lstep : step;
     const bool sample = (mode == 1) || (p.sample_every > 0 && (clock + 1) % p.sample_every == 0);
-    if (sample) {
-        for (int inst = threadIdx.x; inst < p.n_instances; inst += blockDim.x) {
-            const DevInstance I = b.inst[inst];
-            double tot[kObsFields];
-            for (int k = 0; k < kObsFields; ++k) tot[k] = 0.0;
-            for (int blk = I.obs_block_begin; blk < I.obs_block_begin + I.obs_block_count; ++blk)
-                for (int k = 0; k < kObsFields; ++k) tot[k] += b.obs_partial[int64_t(blk) * kObsFields + k];
-            double rec[TTS_NOBS];
-            for (int k = 0; k < TTS_NOBS; ++k) rec[k] = 0.0;
-            // a moving lattice has advanced the spin-step counter already
-            const int64_t sstep = (mode == 0 && !p.lattice_on) ? step + 1 : step;
-            rec[0] = double(sstep) * p.dt;
-            double musum = 0.0, mux = 0.0, muy = 0.0, muz = 0.0;
-            for (int t = 0; t < TTS_MAX_SPECIES; ++t) {
-                const double *a = tot + 12 * t;
-                const double cnt = a[0];
-                if (cnt > 0.0) {
-                    rec[1 + 3 * t] = a[1] / cnt;
-                    rec[2 + 3 * t] = a[2] / cnt;
-                    rec[3 + 3 * t] = a[3] / cnt;
-                    const double m = p.sp[t].mu / kBohrMagneton;
-                    musum += m * cnt;
-                    mux += m * a[1];
-                    muy += m * a[2];
-                    muz += m * a[3];
-                }
-                rec[10] += a[7];
-                rec[11] += a[8];
-                rec[12] += a[9];
-                rec[13 + t] = (cnt > 0.0 && a[11] != 0.0) ? a[10] / (2.0 * kBoltzmann * a[11]) : 0.0;
-            }
-            rec[7] = mux / musum;
-            rec[8] = muy / musum;
-            rec[9] = muz / musum;
-            double te = 0.0, tl = 0.0;
-            for (int c = 0; c < I.ncells; ++c) {
-                te += b.Te[I.cell_begin + c];
-                tl += b.Tl[I.cell_begin + c];
-            }
-            rec[15] = te / I.ncells;
-            rec[16] = tl / I.ncells;
-            if (p.lattice_on && mode == 0) {
-                double ek = 0.0, em = 0.0;
-                for (int blk = I.obs_block_begin; blk < I.obs_block_begin + I.obs_block_count; ++blk) {
-                    ek += p.lat_partial[2 * int64_t(blk)];
-                    em += p.lat_partial[2 * int64_t(blk) + 1];
-                }
-                rec[16] = 2.0 * ek / (3.0 * double(I.n) * kBoltzmann);
-                rec[17] = ek;
-                rec[18] = em;
-            }
-            rec[19] = double(sstep);
-            double *dst;
-            if (mode == 0) {
-                const int64_t k = b.obs_count[inst];
-                dst = b.obs_ring + (int64_t(inst) * p.obs_capacity + (k % p.obs_capacity)) * TTS_NOBS;
-                b.obs_count[inst] = k + 1;
-            } else {
-                dst = b.obs_now + int64_t(inst) * TTS_NOBS;
-            }
-            for (int k = 0; k < TTS_NOBS; ++k) dst[k] = rec[k];
+    if (!sample) return;
+    const int inst = blockIdx.x;
+    const DevInstance I = b.inst[inst];
+    // fixed order: thread j sums blocks j, j + blockDim, ... (and TTM cells,
+    // lattice partials likewise); then a tree.  Extra fields: sum T_e, sum
+    // T_l, kinetic and pair energy.
+    constexpr int NF = kObsFields + 4;
+    __shared__ double red[NF][128];
+    double part[NF];
+    for (int k = 0; k < NF; ++k) part[k] = 0.0;
+    for (int blk = I.obs_block_begin + threadIdx.x; blk < I.obs_block_begin + I.obs_block_count; blk += blockDim.x) {
+        for (int k = 0; k < kObsFields; ++k) part[k] += b.obs_partial[int64_t(blk) * kObsFields + k];
+        if (p.lattice_on && mode == 0) {
+            part[kObsFields + 2] += p.lat_partial[2 * int64_t(blk)];
+            part[kObsFields + 3] += p.lat_partial[2 * int64_t(blk) + 1];
         }
     }
+    for (int c = threadIdx.x; c < I.ncells; c += blockDim.x) {
+        part[kObsFields] += b.Te[I.cell_begin + c];
+        part[kObsFields + 1] += b.Tl[I.cell_begin + c];
+    }
+    for (int k = 0; k < NF; ++k) red[k][threadIdx.x] = part[k];
     __syncthreads();
-    if (mode == 0 && !p.lattice_on && threadIdx.x == 0) *b.step = step + 1;
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < NF; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    double tot[kObsFields];
+    for (int k = 0; k < kObsFields; ++k) tot[k] = red[k][0];
+    double rec[TTS_NOBS];
+    for (int k = 0; k < TTS_NOBS; ++k) rec[k] = 0.0;
+    // a moving lattice has advanced the spin-step counter already
+    const int64_t sstep = (mode == 0 && !p.lattice_on) ? step + 1 : step;
+    rec[0] = double(sstep) * p.dt;
+    double musum = 0.0, mux = 0.0, muy = 0.0, muz = 0.0;
+    for (int t = 0; t < TTS_MAX_SPECIES; ++t) {
+        const double *a = tot + 12 * t;
+        const double cnt = a[0];
+        if (cnt > 0.0) {
+            rec[1 + 3 * t] = a[1] / cnt;
+            rec[2 + 3 * t] = a[2] / cnt;
+            rec[3 + 3 * t] = a[3] / cnt;
+            const double m = p.sp[t].mu / kBohrMagneton;
+            musum += m * cnt;
+            mux += m * a[1];
+            muy += m * a[2];
+            muz += m * a[3];
+        }
+        rec[10] += a[7];
+        rec[11] += a[8];
+        rec[12] += a[9];
+        rec[13 + t] = (cnt > 0.0 && a[11] != 0.0) ? a[10] / (2.0 * kBoltzmann * a[11]) : 0.0;
+    }
+    rec[7] = mux / musum;
+    rec[8] = muy / musum;
+    rec[9] = muz / musum;
+    rec[15] = red[kObsFields][0] / I.ncells;
+    rec[16] = red[kObsFields + 1][0] / I.ncells;
+    if (p.lattice_on && mode == 0) {
+        const double ek = red[kObsFields + 2][0], em = red[kObsFields + 3][0];
+        rec[16] = 2.0 * ek / (3.0 * double(I.n) * kBoltzmann);
+        rec[17] = ek;
+        rec[18] = em;
+    }
+    rec[19] = double(sstep);
+    double *dst;
+    if (mode == 0) {
+        const int64_t k = b.obs_count[inst];
+        dst = b.obs_ring + (int64_t(inst) * p.obs_capacity + (k % p.obs_capacity)) * TTS_NOBS;
+        b.obs_count[inst] = k + 1;
+    } else {
+        dst = b.obs_now + int64_t(inst) * TTS_NOBS;
+    }
+    for (int k = 0; k < TTS_NOBS; ++k) dst[k] = rec[k];
 }
 
+__global__ void step_inc_kernel(int64_t *step) { *step += 1; }
+
 // ---------------------------------------------------------------------------
-// Source calibration, one block per job.  The TTM-only run uses the same
-// update as ttm_kernel; every thread keeps the running maximum of its cells
-// and the block reduces it once per run.
+// Source calibration.  The TTM-only run uses the same update as ttm_kernel;
+// every thread keeps the running maximum of its cells and the block reduces
+// it once per run.
 // ---------------------------------------------------------------------------
-__device__ double calib_peak(CalibJob &J, double P0, double dt, const TtmParams &tp, double *red)
+__device__ double calib_peak(const CalibJob &J, double P0, double dt, const TtmParams &tp, double *work, double *red)
 {
     const int nx = J.cells[0], ny = J.cells[1], nz = J.cells[2], nc = nx * ny * nz;
-    double *Te = J.work, *Tl = J.work + nc, *dE = J.work + 2 * nc;
+    double *Te = work, *Tl = work + nc, *dE = work + 2 * nc;
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
         Te[c] = tp.T0;
         Tl[c] = tp.T0;
@@ -456,27 +527,25 @@ __device__ double calib_peak(CalibJob &J, double P0, double dt, const TtmParams 
     return r;
 }
 
-__global__ void calibrate_kernel(CalibJob *jobs, double dt, TtmParams tp)
+// one CTA per (job, candidate power): the peak of a TTM-only run
+__global__ void calibrate_kernel(const CalibJob *jobs, const double *cand, double *peaks, int ncand, double dt,
+                                 TtmParams tp, int64_t work_per_block)
 {
-    __shared__ double red[256];
-    CalibJob &J = jobs[blockIdx.x];
-    double hi = J.guess;
-    // at most 200 doublings: the peak grows without bound with P0
-    for (int it = 0; it < 200 && calib_peak(J, hi, dt, tp, red) < J.target; ++it) hi *= 2.0;
-    double lo = 0.0;
-    for (int it = 0; it < 60; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (calib_peak(J, mid, dt, tp, red) < J.target) lo = mid; else hi = mid;
-    }
-    if (threadIdx.x == 0) J.P0 = 0.5 * (lo + hi);
+    __shared__ double red[1024];
+    const int job = blockIdx.x / ncand;
+    const CalibJob J = jobs[job];
+    const double pk = calib_peak(J, cand[blockIdx.x], dt, tp, J.work + work_per_block * (blockIdx.x % ncand), red);
+    if (threadIdx.x == 0) peaks[blockIdx.x] = pk;
 }
 
 }  // namespace
 
-cudaError_t launch_calibrate(CalibJob *jobs_dev, int njobs, int ncells, double dt, const TtmParams &tp, cudaStream_t st)
+cudaError_t launch_calibrate(const CalibJob *jobs_dev, const double *cand_dev, double *peaks_dev, int njobs,
+                             int ncand, int ncells, double dt, const TtmParams &tp, cudaStream_t st)
 {
     if (njobs <= 0) return cudaSuccess;
-    calibrate_kernel<<<njobs, ncells <= 32 ? 32 : 256, 0, st>>>(jobs_dev, dt, tp);
+    const int bs = ncells <= 32 ? 32 : (ncells <= 256 ? 256 : 1024);
+    calibrate_kernel<<<njobs * ncand, bs, 0, st>>>(jobs_dev, cand_dev, peaks_dev, ncand, dt, tp, 3 * int64_t(ncells));
     return cudaGetLastError();
 }
 
@@ -492,10 +561,10 @@ cudaError_t launch_sigma(const StepParams &p, const DevBuffers &b, int ncells, i
 }
 
 cudaError_t launch_pass_general(const StepParams &p, const DevBuffers &b, int precision, int pass,
-                                int64_t range_offset, int nranges, int64_t nwork, cudaStream_t st)
+                                int64_t range_offset, int nranges, int64_t nwork, cudaStream_t st, int block)
 {
     if (nwork <= 0) return cudaSuccess;
-    const int bs = 256;
+    const int bs = block;
     const int64_t gs = (nwork + bs - 1) / bs;
     if (precision == 64)
         pass_general_kernel<double><<<gs, bs, 0, st>>>(p, b, pass, b.ranges + range_offset, nranges, nwork);
@@ -505,22 +574,120 @@ cudaError_t launch_pass_general(const StepParams &p, const DevBuffers &b, int pr
 }
 
 cudaError_t launch_ttm(const StepParams &p, const DevBuffers &b, const TtmParams &tp, int n_instances,
-                       cudaStream_t st)
+                       cudaStream_t st, int precision, int inc_step)
 {
+    if (b.cell_inst && p.ttm_one_substep) {
+        const int n = p.ncells_total;
+        ttm_increment_kernel<<<(n + 255) / 256, 256, 0, st>>>(p, b, tp, b.cell_inst, n);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (precision == 64)
+            ttm_apply_kernel<double><<<(n + 255) / 256, 256, 0, st>>>(p, b, tp, n, inc_step);
+        else
+            ttm_apply_kernel<float><<<(n + 255) / 256, 256, 0, st>>>(p, b, tp, n, inc_step);
+        return cudaGetLastError();
+    }
     ttm_kernel<<<n_instances, 256, 0, st>>>(p, b, tp);
     return cudaGetLastError();
 }
 
-cudaError_t launch_obs(const StepParams &p, const DevBuffers &b, int precision, int nblocks, int mode,
-                       cudaStream_t st)
+cudaError_t launch_obs(StepParams p, const DevBuffers &b, int precision, int nblocks, int mode, cudaStream_t st)
 {
+    const int grid = nblocks < 1184 ? nblocks : 1184;    // 8 CTAs per SM on 148 SMs
+    p.obs_blocks = nblocks;
     if (precision == 64)
-        obs_partial_kernel<double><<<nblocks, kObsBlock, 0, st>>>(p, b, mode);
+        obs_partial_kernel<double><<<grid, kObsBlock, 0, st>>>(p, b, mode);
     else
-        obs_partial_kernel<float><<<nblocks, kObsBlock, 0, st>>>(p, b, mode);
+        obs_partial_kernel<float><<<grid, kObsBlock, 0, st>>>(p, b, mode);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    obs_final_kernel<<<1, 256, 0, st>>>(p, b, mode);
+    return launch_obs_reduce(p, b, mode, st);
+}
+
+cudaError_t launch_obs_reduce(const StepParams &p, const DevBuffers &b, int mode, cudaStream_t st)
+{
+    obs_reduce_kernel<<<p.n_instances, 128, 0, st>>>(p, b, mode);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || mode != 0 || p.lattice_on) return e;
+    step_inc_kernel<<<1, 1, 0, st>>>(b.step);
+    return cudaGetLastError();
+}
+
+namespace {
+// instance of a slot: the last instance whose first slot is <= slot
+__device__ __forceinline__ int slot_instance(const DevInstance *inst, int n_inst, int64_t slot)
+{
+    int lo = 0, hi = n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (inst[mid].slot_begin <= slot) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename R>
+__global__ void spins_to_atoms_kernel(const R *__restrict__ sx, const R *__restrict__ sy, const R *__restrict__ sz,
+                                      const int *__restrict__ atom, const DevInstance *inst, int n_inst,
+                                      int64_t n_total, R *out)
+{
+    const int64_t slot = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (slot >= n_total) return;
+    const int64_t g = inst[slot_instance(inst, n_inst, slot)].slot_begin + atom[slot];
+    out[3 * g] = sx[slot];
+    out[3 * g + 1] = sy[slot];
+    out[3 * g + 2] = sz[slot];
+}
+
+template <typename R>
+__global__ void spins_from_atoms_kernel(R *sx, R *sy, R *sz, const int *__restrict__ atom, const DevInstance *inst,
+                                        int n_inst, int64_t n_total, const R *__restrict__ in)
+{
+    const int64_t slot = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (slot >= n_total) return;
+    const int64_t g = inst[slot_instance(inst, n_inst, slot)].slot_begin + atom[slot];
+    sx[slot] = in[3 * g];
+    sy[slot] = in[3 * g + 1];
+    sz[slot] = in[3 * g + 2];
+}
+}  // namespace
+
+cudaError_t launch_spins_to_atoms(const DevBuffers &b, int64_t n_total, int n_inst, int precision, void *out,
+                                  cudaStream_t st)
+{
+    const int bs = 256;
+    const int64_t gs = (n_total + bs - 1) / bs;
+    if (precision == 64)
+        spins_to_atoms_kernel<double><<<gs, bs, 0, st>>>(static_cast<const double *>(b.sx),
+                                                         static_cast<const double *>(b.sy),
+                                                         static_cast<const double *>(b.sz), b.atom, b.inst, n_inst,
+                                                         n_total, static_cast<double *>(out));
+    else
+        spins_to_atoms_kernel<float><<<gs, bs, 0, st>>>(static_cast<const float *>(b.sx),
+                                                        static_cast<const float *>(b.sy),
+                                                        static_cast<const float *>(b.sz), b.atom, b.inst, n_inst,
+                                                        n_total, static_cast<float *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spins_from_atoms(const DevBuffers &b, int64_t n_total, int n_inst, int precision, const void *in,
+                                    cudaStream_t st)
+{
+    const int bs = 256;
+    const int64_t gs = (n_total + bs - 1) / bs;
+    if (precision == 64)
+        spins_from_atoms_kernel<double><<<gs, bs, 0, st>>>(static_cast<double *>(b.sx), static_cast<double *>(b.sy),
+                                                           static_cast<double *>(b.sz), b.atom, b.inst, n_inst,
+                                                           n_total, static_cast<const double *>(in));
+    else
+        spins_from_atoms_kernel<float><<<gs, bs, 0, st>>>(static_cast<float *>(b.sx), static_cast<float *>(b.sy),
+                                                          static_cast<float *>(b.sz), b.atom, b.inst, n_inst, n_total,
+                                                          static_cast<const float *>(in));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_inc(const DevBuffers &b, cudaStream_t st)
+{
+    step_inc_kernel<<<1, 1, 0, st>>>(b.step);
     return cudaGetLastError();
 }
 

@@ -22,6 +22,8 @@ struct StepParams {
     int obs_capacity;
     int ncells_total;        // TTM cells over all instances (host-side launch size)
     int obs_blocks;          // observable partial blocks (host-side launch size)
+    int ttm_one_substep;     // every TTM grid advances in one sub-step per step
+    int sigma_per_step;      // the noise table is rebuilt by its own kernel every step
     int lattice_on;          // observables of a moving lattice (sampled per lattice step)
     int64_t *lstep;          // lattice step counter (moving lattice)
     double *lat_partial;     // per observable block: kinetic and pair energy (moving lattice)
@@ -50,10 +52,39 @@ struct DevBuffers {
     double *obs_ring = nullptr;   // n_instances * capacity * TTS_NOBS
     int64_t *obs_count = nullptr; // samples taken per instance
     double *obs_now = nullptr;    // n_instances * TTS_NOBS
+    int *cell_inst = nullptr;     // instance of each TTM cell
 };
 
 constexpr int kObsFields = 24;       // per species: 12 partial sums
 constexpr int kObsBlock = 128;       // threads of an observable block
+constexpr int kObsSpan = 1024;       // slots of an observable block (8 a thread)
+
+#ifdef __CUDACC__
+// Sum v over the block's kObsBlock threads into out[k] for k < NF: shuffles within each
+// warp, then warp 0's lanes add the warps' sums in warp order (a fixed order,
+// so the result does not depend on timing).
+template <int NF>
+__device__ __forceinline__ void block_sum_store(const double (&v)[NF], double *out)
+{
+    __shared__ double wsum[kObsBlock / 32][NF];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) wsum[warp][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NF) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kObsBlock / 32; ++w) t += wsum[w][threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+#endif
 
 enum HealthBits : unsigned int {
     kHealthNonFinite = 1u,
@@ -66,28 +97,42 @@ enum HealthBits : unsigned int {
 cudaError_t launch_sigma(const StepParams &p, const DevBuffers &b, int ncells_total, int precision,
                          cudaStream_t st);
 cudaError_t launch_pass_general(const StepParams &p, const DevBuffers &b, int precision, int pass,
-                                int64_t range_offset, int nranges, int64_t nwork, cudaStream_t st);
+                                int64_t range_offset, int nranges, int64_t nwork, cudaStream_t st, int block = 256);
+// TTM advance of every instance; with one sub-step per step the grid-parallel
+// path also refreshes the noise table for the next step and, with inc_step,
+// advances the step counter.
 cudaError_t launch_ttm(const StepParams &p, const DevBuffers &b, const TtmParams &tp, int n_instances,
-                       cudaStream_t st);
-cudaError_t launch_obs(const StepParams &p, const DevBuffers &b, int precision, int nblocks, int mode,
-                       cudaStream_t st);
+                       cudaStream_t st, int precision, int inc_step);
+cudaError_t launch_step_inc(const DevBuffers &b, cudaStream_t st);
+// partials_done: the engine has written this step's observable partial sums.
+cudaError_t step_tail(const StepParams &p, const DevBuffers &b, const TtmParams &tp, bool ttm_active, int n_inst,
+                      int precision, int obs_blocks, cudaStream_t st, int *kernels, bool partials_done = false);
+cudaError_t launch_obs(StepParams p, const DevBuffers &b, int precision, int nblocks, int mode, cudaStream_t st);
+// General SoA (slot order) <-> xyz interleaved in canonical atom order of
+// every instance (global index = slot_begin of the slot's instance + atom id).
+cudaError_t launch_spins_to_atoms(const DevBuffers &b, int64_t n_total, int n_inst, int precision, void *out,
+                                  cudaStream_t st);
+cudaError_t launch_spins_from_atoms(const DevBuffers &b, int64_t n_total, int n_inst, int precision, const void *in,
+                                    cudaStream_t st);
+// The per-instance reduction of the partial sums (and, mode 0, the step
+// increment) alone.
+cudaError_t launch_obs_reduce(const StepParams &p, const DevBuffers &b, int mode, cudaStream_t st);
 
-// One source-power calibration: find P0 such that the largest T_e over the
-// cells and the step times t_n of a TTM-only run (to t0 + 10 sigma_t) equals
-// `target`, by 60 bisection steps after doubling an initial upper bound.
+// Source-power calibration: P0 such that the largest T_e over the cells and
+// the step times t_n of a TTM-only run (to t0 + 10 sigma_t) equals the target.
+// Each launch evaluates ncand candidate powers per job, one CTA each; the host
+// narrows the bracket (multi-section) until it is at double resolution.
 struct CalibJob {
     int cells[3];
     int substeps;
     double dx[3];
     double sigma_t, t0;
-    double target;
-    double guess;              // initial upper bound
     int64_t nsteps;            // step times to scan
     const double *shape;       // per cell source profile (device)
-    double *work;              // 3 * ncells doubles of device scratch
-    double P0;                 // result
+    double *work;              // ncand * 3 * ncells doubles of device scratch
 };
 
-cudaError_t launch_calibrate(CalibJob *jobs_dev, int njobs, int ncells, double dt, const TtmParams &tp, cudaStream_t st);
+cudaError_t launch_calibrate(const CalibJob *jobs_dev, const double *cand_dev, double *peaks_dev, int njobs,
+                             int ncand, int ncells, double dt, const TtmParams &tp, cudaStream_t st);
 
 }  // namespace tts

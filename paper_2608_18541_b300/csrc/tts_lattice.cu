@@ -341,13 +341,14 @@ __global__ void __launch_bounds__(kObsBlock) lattice_energy_kernel(LatArgs a, De
     if (a.sample_every <= 0 || (*a.lstep + 1) % a.sample_every != 0) return;
     const int inst = b.obs_block_inst[blockIdx.x];
     const DevInstance I = b.inst[inst];
-    const int64_t i = b.obs_block_begin[blockIdx.x] + threadIdx.x;
-    double ek = 0.0, em = 0.0;
-    if (i < I.slot_begin + I.n) {
-        const R *ux = arr<R>(a.u, 0, a.n), *uy = arr<R>(a.u, 1, a.n), *uz = arr<R>(a.u, 2, a.n);
+    double e[2] = {0.0, 0.0};    // kinetic, pair
+    const R *ux = arr<R>(a.u, 0, a.n), *uy = arr<R>(a.u, 1, a.n), *uz = arr<R>(a.u, 2, a.n);
+    for (int jj = 0; jj < kObsSpan / kObsBlock; ++jj) {
+        const int64_t i = b.obs_block_begin[blockIdx.x] + threadIdx.x + int64_t(jj) * kObsBlock;
+        if (i >= I.slot_begin + I.n) break;
         for (int c = 0; c < 3; ++c) {
             const double v = arr<R>(a.v, c, a.n)[i];
-            ek += 0.5 * a.mass * v * v;
+            e[0] += 0.5 * a.mass * v * v;
         }
         for (int k = 0; k < a.zc; ++k) {
             const int j = a.cand[int64_t(k) * a.n + i];
@@ -356,24 +357,10 @@ __global__ void __launch_bounds__(kObsBlock) lattice_energy_kernel(LatArgs a, De
             const double dy = double(cv<R>(a, 1, k, i)) + double(uy[j]) - double(uy[i]);
             const double dz = double(cv<R>(a, 2, k, i)) + double(uz[j]) - double(uz[i]);
             const double r = sqrt(dx * dx + dy * dy + dz * dz);
-            if (r < a.morse_rc) em += 0.5 * (morse_U_raw(a, r) - a.U_rc - (r - a.morse_rc) * a.dU_rc);
+            if (r < a.morse_rc) e[1] += 0.5 * (morse_U_raw(a, r) - a.U_rc - (r - a.morse_rc) * a.dU_rc);
         }
     }
-    __shared__ double red[2][kObsBlock];
-    red[0][threadIdx.x] = ek;
-    red[1][threadIdx.x] = em;
-    __syncthreads();
-    for (int s = kObsBlock / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            red[0][threadIdx.x] += red[0][threadIdx.x + s];
-            red[1][threadIdx.x] += red[1][threadIdx.x + s];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        a.lat_partial[2 * int64_t(blockIdx.x)] = red[0][0];
-        a.lat_partial[2 * int64_t(blockIdx.x) + 1] = red[1][0];
-    }
+    block_sum_store<2>(e, a.lat_partial + 2 * int64_t(blockIdx.x));
 }
 
 __global__ void inc_kernel(int64_t *counter) { *counter += 1; }
@@ -505,6 +492,43 @@ int64_t lattice_units_per_step(const tts_system *s) { return s->lat ? s->n_total
 
 double lattice_step_length(const tts_system *s) { return s->lat ? s->lat->dtL : s->desc.dt; }
 
+// Checkpoint part of a moving lattice: lattice step, u, v, f (3 x n each,
+// spin precision), per-cell tallies.  With buf == nullptr only the size.
+size_t lattice_state_bytes(const tts_system *s)
+{
+    if (!s->lat) return 0;
+    return sizeof(int64_t) + 9 * size_t(s->n_total) * s->rsize + size_t(s->lat->ncells_alloc) * sizeof(long long);
+}
+
+int lattice_state_io(tts_system *s, char *buf, bool save)
+{
+    LatticeState *L = s->lat;
+    if (!L) return TTS_OK;
+    const cudaMemcpyKind k = save ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice;
+    auto io = [&](void *dev, size_t bytes) -> cudaError_t {
+        cudaError_t e = save ? cudaMemcpy(buf, dev, bytes, k) : cudaMemcpy(dev, buf, bytes, k);
+        buf += bytes;
+        return e;
+    };
+    const size_t arr = 3 * size_t(s->n_total) * s->rsize;
+    cudaError_t e = io(L->lstep, sizeof(int64_t));
+    if (e == cudaSuccess) e = io(L->u, arr);
+    if (e == cudaSuccess) e = io(L->v, arr);
+    if (e == cudaSuccess) e = io(L->f, arr);
+    if (e == cudaSuccess && L->ncells_alloc > 0) e = io(L->cell_acc, size_t(L->ncells_alloc) * sizeof(long long));
+    if (e != cudaSuccess) return cuda_fail(e, "lattice state");
+    // the exchange table and bath cells follow the restored positions
+    return save ? TTS_OK : lattice_refresh_tables(s);
+}
+
+int lattice_refresh_tables(tts_system *s)
+{
+    cudaError_t e = per_atom(s, s->stream, 2);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    ++s->launches;
+    return e == cudaSuccess ? TTS_OK : cuda_fail(e, "lattice refresh");
+}
+
 // recompute the exchange table, cells and forces for the current state
 int lattice_refresh_now(tts_system *s)
 {
@@ -542,7 +566,7 @@ cudaError_t lattice_record_step(tts_system *s, cudaStream_t st, int *kernels, cu
             for (int pass = 0; pass < s->max_passes && e == cudaSuccess; ++pass) {
                 const int64_t off = s->pass_offset[pass];
                 const int nr = static_cast<int>(s->pass_offset[pass + 1] - off);
-                e = launch_pass_general(s->p, s->b, s->precision, pass, off, nr, s->pass_work[pass], st);
+                e = launch_pass_general(s->p, s->b, s->precision, pass, off, nr, s->pass_work[pass], st, s->pass_block);
                 ++*kernels;
             }
             if (e == cudaSuccess) {

@@ -5,7 +5,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -52,7 +54,8 @@ void free_buffers(tts_system *s)
     DevBuffers &b = s->b;
     void *ptrs[] = {b.sx, b.sy, b.sz, b.atom, b.species, b.cell, b.nbr, b.nbr_w, b.sigma, b.Te, b.Tl,
                     b.src_shape, b.ttm_scratch, b.src_energy, b.inst, b.ranges, b.step, b.health,
-                    b.obs_partial, b.obs_block_inst, b.obs_block_begin, b.obs_ring, b.obs_count, b.obs_now};
+                    b.obs_partial, b.obs_block_inst, b.obs_block_begin, b.obs_ring, b.obs_count, b.obs_now,
+                    b.cell_inst};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     s->b = DevBuffers{};
@@ -196,15 +199,17 @@ int upload_general(tts_system *s)
 int alloc_cells(tts_system *s, int ncells_total)
 {
     DevBuffers &b = s->b;
-    for (void *q : {(void *)b.Te, (void *)b.Tl, (void *)b.src_shape, (void *)b.ttm_scratch, b.sigma})
+    for (void *q : {(void *)b.Te, (void *)b.Tl, (void *)b.src_shape, (void *)b.ttm_scratch, b.sigma, (void *)b.cell_inst})
         if (q) cudaFree(q);
     b.Te = b.Tl = b.src_shape = b.ttm_scratch = nullptr;
     b.sigma = nullptr;
+    b.cell_inst = nullptr;
     int rc;
     if ((rc = dev_alloc(&b.Te, ncells_total, "T_e"))) return rc;
     if ((rc = dev_alloc(&b.Tl, ncells_total, "T_l"))) return rc;
     if ((rc = dev_alloc(&b.src_shape, ncells_total, "source shape"))) return rc;
     if ((rc = dev_alloc(&b.ttm_scratch, 2 * size_t(ncells_total), "TTM scratch"))) return rc;
+    if ((rc = dev_alloc(&b.cell_inst, ncells_total, "cell instances"))) return rc;
     char *sig = nullptr;
     if ((rc = dev_alloc(&sig, size_t(ncells_total) * TTS_MAX_SPECIES * 2 * s->rsize, "sigma table"))) return rc;
     b.sigma = sig;
@@ -221,37 +226,31 @@ cudaError_t record_step(tts_system *s, cudaStream_t c, int *kernels, cudaEvent_t
     if (s->lat) return lattice_record_step(s, c, kernels, ev0, ev1);
     if (s->eng) return engine_record_step(s->eng, s->p, s->b, s->tp, s->ttm_active, c, kernels, ev0, ev1);
     // general engine
-    cudaError_t e = launch_sigma(s->p, s->b, s->ncells_total, s->precision, c);
-    ++*kernels;
+    cudaError_t e = cudaSuccess;
+    if (s->p.sigma_per_step) {
+        e = launch_sigma(s->p, s->b, s->ncells_total, s->precision, c);
+        ++*kernels;
+    }
     if (e == cudaSuccess && ev0) e = cudaEventRecord(ev0, c);
     for (int pass = 0; pass < s->max_passes && e == cudaSuccess; ++pass) {
         const int64_t off = s->pass_offset[pass];
         const int nr = static_cast<int>(s->pass_offset[pass + 1] - off);
-        e = launch_pass_general(s->p, s->b, s->precision, pass, off, nr, s->pass_work[pass], c);
+        e = launch_pass_general(s->p, s->b, s->precision, pass, off, nr, s->pass_work[pass], c, s->pass_block);
         ++*kernels;
     }
     if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, c);
-    if (e == cudaSuccess && s->ttm_active) {
-        e = launch_ttm(s->p, s->b, s->tp, s->n_inst, c);
-        ++*kernels;
-    }
-    if (e == cudaSuccess) {
-        e = launch_obs(s->p, s->b, s->precision, s->obs_blocks, 0, c);
-        *kernels += 2;
-    }
+    e = (e == cudaSuccess) ? step_tail(s->p, s->b, s->tp, s->ttm_active, s->n_inst, s->precision, s->obs_blocks, c, kernels)
+                           : e;
     return e;
 }
 
-int build_graph(tts_system *s)
+int capture_steps(tts_system *s, int nsteps, cudaGraphExec_t *out, int *kernels_per_step)
 {
-    if (s->graph) {
-        cudaGraphExecDestroy(s->graph);
-        s->graph = nullptr;
-    }
     cudaStream_t c = s->capture;
     TTS_CUDA(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal), "begin capture");
     int kernels = 0;
-    cudaError_t e = record_step(s, c, &kernels, nullptr, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < nsteps && e == cudaSuccess; ++i) e = record_step(s, c, &kernels, nullptr, nullptr);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c, &g);
     if (e != cudaSuccess) {
@@ -259,10 +258,27 @@ int build_graph(tts_system *s)
         return cuda_fail(e, "record step");
     }
     if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
-    e = cudaGraphInstantiate(&s->graph, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "instantiate step graph");
-    s->kernels_per_step = kernels;
+    *kernels_per_step = kernels;
+    return TTS_OK;
+}
+
+int build_graph(tts_system *s)
+{
+    for (cudaGraphExec_t *g : {&s->graph, &s->graph_multi})
+        if (*g) {
+            cudaGraphExecDestroy(*g);
+            *g = nullptr;
+        }
+    // a moving lattice has ~100 kernels per step: fewer steps per graph
+    s->graph_steps = s->lat ? 4 : 16;
+    int k1 = 0, km = 0;
+    int rc = capture_steps(s, 1, &s->graph, &k1);
+    if (!rc) rc = capture_steps(s, s->graph_steps, &s->graph_multi, &km);
+    if (rc) return rc;
+    s->kernels_per_step = k1;
     s->dirty = false;
     return TTS_OK;
 }
@@ -272,6 +288,48 @@ void drop_profile_events(tts_system *s)
     for (cudaEvent_t ev : s->prof_events) cudaEventDestroy(ev);
     s->prof_events.clear();
     s->prof_pair_steps.clear();
+}
+
+}  // namespace
+
+// End of a step for the general and checker engines: TTM, then either the
+// observable kernels (which advance the step counter) or a bare increment,
+// folded into the TTM update when that runs on the grid-parallel path.
+cudaError_t tts::step_tail(const StepParams &p, const DevBuffers &b, const TtmParams &tp, bool ttm_active, int n_inst,
+                           int precision, int obs_blocks, cudaStream_t st, int *kernels, bool partials_done)
+{
+    const bool sampling = p.sample_every > 0;
+    const bool fold = ttm_active && p.ttm_one_substep && !sampling;
+    cudaError_t e = cudaSuccess;
+    if (ttm_active) {
+        e = launch_ttm(p, b, tp, n_inst, st, precision, fold ? 1 : 0);
+        *kernels += p.ttm_one_substep ? 2 : 1;
+    }
+    if (e != cudaSuccess) return e;
+    if (sampling && partials_done) {
+        e = launch_obs_reduce(p, b, 0, st);
+        *kernels += 2;
+    } else if (sampling) {
+        e = launch_obs(p, b, precision, obs_blocks, 0, st);
+        *kernels += 3;
+    } else if (!fold) {
+        e = launch_step_inc(b, st);
+        *kernels += 1;
+    }
+    return e;
+}
+
+namespace {
+
+// Noise table from the current T_e (after creation and every change of state
+// that the per-step kernels do not see).
+int refresh_sigma(tts_system *s)
+{
+    if (!s->b.sigma) return TTS_OK;
+    cudaError_t e = launch_sigma(s->p, s->b, s->ncells_total, s->precision, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    ++s->launches;
+    return e == cudaSuccess ? TTS_OK : cuda_fail(e, "noise table");
 }
 
 int check_inst(tts_system *s, int inst)
@@ -351,9 +409,11 @@ int tts_destroy(tts_system *s)
     if (!s) return TTS_OK;
     cudaStreamSynchronize(s->stream);
     if (s->graph) cudaGraphExecDestroy(s->graph);
+    if (s->graph_multi) cudaGraphExecDestroy(s->graph_multi);
     drop_profile_events(s);
     if (s->eng) engine_destroy(s->eng);
     if (s->lat) lattice_destroy(s->lat);
+    if (s->io_buf) cudaFree(s->io_buf);
     free_buffers(s);
     if (s->capture) cudaStreamDestroy(s->capture);
     delete s;
@@ -426,7 +486,7 @@ int tts_create_system(const tts_system_desc *desc, void *stream, tts_system **ou
         di.substeps = 1;
         di.sigma_t = 1.0;
         di.obs_block_begin = obs_block;
-        di.obs_block_count = static_cast<int>((hi.n + kObsBlock - 1) / kObsBlock);
+        di.obs_block_count = static_cast<int>((hi.n + kObsSpan - 1) / kObsSpan);
         obs_block += di.obs_block_count;
         slot += hi.n;
         s->max_colours = std::max(s->max_colours, hi.ncolours);
@@ -546,7 +606,7 @@ int tts_create_system(const tts_system_desc *desc, void *stream, tts_system **ou
         for (int i = 0; i < s->n_inst; ++i)
             for (int k = 0; k < s->dinst[i].obs_block_count; ++k) {
                 bi[s->dinst[i].obs_block_begin + k] = i;
-                bb[s->dinst[i].obs_block_begin + k] = s->dinst[i].slot_begin + int64_t(k) * kObsBlock;
+                bb[s->dinst[i].obs_block_begin + k] = s->dinst[i].slot_begin + int64_t(k) * kObsSpan;
             }
         if ((rc = upload(b.obs_block_inst, bi.data(), bi.size() * sizeof(int), s->stream, "upload obs blocks"))) return rc;
         if ((rc = upload(b.obs_block_begin, bb.data(), bb.size() * sizeof(int64_t), s->stream, "upload obs blocks"))) return rc;
@@ -567,6 +627,8 @@ int tts_create_system(const tts_system_desc *desc, void *stream, tts_system **ou
         rc = engine_create(*desc, s->host, s->slot_of_atom, s->dinst, s->p, s->b, s->engine, s->stream, &s->eng);
         if (rc) return fail(rc, std::string("engine set-up failed: ") + engine_last_error());
     }
+    s->p.sigma_per_step = 0;                 // uniform bath: the table never changes
+    if ((rc = refresh_sigma(s.get()))) return rc;
     *out = s.release();
     return TTS_OK;
 }
@@ -648,19 +710,30 @@ int tts_set_ttm_grid(tts_system *s, const tts_ttm_desc *t)
     tp.depth_z = t->depth_z;
     if (!keys.empty()) {
         const int nj = static_cast<int>(keys.size());
+        const int NC = 32;                       // candidate powers per job and round
         std::vector<int> first(nj, -1);
         for (int i = 0; i < s->n_inst; ++i)
             if (job_of[i] >= 0 && first[job_of[i]] < 0) first[job_of[i]] = i;
         std::vector<CalibJob> jobs(nj);
-        double *shape_dev = nullptr, *work_dev = nullptr;
+        double *shape_dev = nullptr, *work_dev = nullptr, *cand_dev = nullptr, *peak_dev = nullptr;
         CalibJob *jobs_dev = nullptr;
-        if ((rc = dev_alloc(&shape_dev, size_t(nj) * nc, "calibration shapes")) ||
-            (rc = dev_alloc(&work_dev, size_t(nj) * 3 * nc, "calibration scratch")) ||
-            (rc = dev_alloc(&jobs_dev, nj, "calibration jobs"))) {
+        auto release = [&]() {
             cudaFree(shape_dev);
             cudaFree(work_dev);
+            cudaFree(jobs_dev);
+            cudaFree(cand_dev);
+            cudaFree(peak_dev);
+        };
+        if ((rc = dev_alloc(&shape_dev, size_t(nj) * nc, "calibration shapes")) ||
+            (rc = dev_alloc(&work_dev, size_t(nj) * NC * 3 * nc, "calibration scratch")) ||
+            (rc = dev_alloc(&jobs_dev, nj, "calibration jobs")) ||
+            (rc = dev_alloc(&cand_dev, size_t(nj) * NC, "calibration candidates")) ||
+            (rc = dev_alloc(&peak_dev, size_t(nj) * NC, "calibration peaks"))) {
+            release();
             return rc;
         }
+        std::vector<double> lo(nj, 0.0), hi(nj, 0.0), guess(nj), cand(size_t(nj) * NC), peaks(size_t(nj) * NC);
+        std::vector<int> bracketed(nj, 0);
         for (int j = 0; j < nj; ++j) {
             const HostTtm &h = hts[first[j]];
             CalibJob &J = jobs[j];
@@ -672,32 +745,84 @@ int tts_set_ttm_grid(tts_system *s, const tts_ttm_desc *t)
             J.substeps = h.substeps;
             J.sigma_t = h.sigma_t;
             J.t0 = h.t0;
-            J.target = keys[j].peak;
-            J.guess = 0.5 * t->gamma_e * (keys[j].peak * keys[j].peak - t->T0 * t->T0) /
-                      (h.sigma_t * std::sqrt(2.0 * M_PI));
             J.nsteps = static_cast<int64_t>(std::ceil((h.t0 + 10.0 * h.sigma_t) / lattice_step_length(s)));
             J.shape = shape_dev + size_t(j) * nc;
-            J.work = work_dev + size_t(j) * 3 * nc;
+            J.work = work_dev + size_t(j) * NC * 3 * nc;
+            guess[j] = 0.5 * t->gamma_e * (keys[j].peak * keys[j].peak - t->T0 * t->T0) /
+                       (h.sigma_t * std::sqrt(2.0 * M_PI));
             cudaMemcpyAsync(shape_dev + size_t(j) * nc, h.shape.data(), nc * sizeof(double), cudaMemcpyHostToDevice,
                             s->stream);
         }
         cudaMemcpyAsync(jobs_dev, jobs.data(), nj * sizeof(CalibJob), cudaMemcpyHostToDevice, s->stream);
-        cudaError_t e = launch_calibrate(jobs_dev, nj, nc, lattice_step_length(s), tp, s->stream);
-        ++s->launches;
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(jobs.data(), jobs_dev, nj * sizeof(CalibJob), cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-        cudaFree(shape_dev);
-        cudaFree(work_dev);
-        cudaFree(jobs_dev);
+        cudaError_t e = cudaSuccess;
+        auto evaluate = [&]() {
+            e = cudaMemcpyAsync(cand_dev, cand.data(), cand.size() * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+            if (e == cudaSuccess) e = launch_calibrate(jobs_dev, cand_dev, peak_dev, nj, NC, nc, lattice_step_length(s), tp, s->stream);
+            ++s->launches;
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(peaks.data(), peak_dev, peaks.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        };
+        // bracket: powers guess * 2^c; the peak grows without bound with P0
+        for (int round = 0; round < 8 && e == cudaSuccess; ++round) {
+            bool all = true;
+            for (int j = 0; j < nj; ++j) {
+                all = all && bracketed[j];
+                for (int c = 0; c < NC; ++c) cand[j * NC + c] = guess[j] * std::ldexp(1.0, c);
+            }
+            if (all) break;
+            evaluate();
+            for (int j = 0; j < nj && e == cudaSuccess; ++j) {
+                if (bracketed[j]) continue;
+                for (int c = 0; c < NC; ++c)
+                    if (peaks[j * NC + c] >= keys[j].peak) {
+                        hi[j] = cand[j * NC + c];
+                        lo[j] = c > 0 ? cand[j * NC + c - 1] : 0.0;
+                        bracketed[j] = 1;
+                        break;
+                    }
+                if (!bracketed[j]) guess[j] = cand[j * NC + NC - 1] * 2.0;
+            }
+        }
+        for (int j = 0; j < nj && e == cudaSuccess; ++j)
+            if (!bracketed[j]) e = cudaErrorInvalidValue;
+        // multi-section: each round splits [lo, hi] into NC + 1 parts
+        for (int round = 0; round < 14 && e == cudaSuccess; ++round) {
+            bool done = true;
+            for (int j = 0; j < nj; ++j) {
+                done = done && (hi[j] - lo[j]) <= 4e-16 * hi[j];   // a few ulps of hi
+                for (int c = 0; c < NC; ++c) cand[j * NC + c] = lo[j] + (hi[j] - lo[j]) * (c + 1) / (NC + 1);
+            }
+            if (done) break;
+            evaluate();
+            for (int j = 0; j < nj && e == cudaSuccess; ++j) {
+                int c = 0;
+                while (c < NC && peaks[j * NC + c] < keys[j].peak) ++c;
+                const double new_lo = c > 0 ? cand[j * NC + c - 1] : lo[j];
+                const double new_hi = c < NC ? cand[j * NC + c] : hi[j];
+                lo[j] = new_lo;
+                hi[j] = new_hi;
+            }
+        }
+        release();
         if (e != cudaSuccess) return cuda_fail(e, "source calibration");
         for (int i = 0; i < s->n_inst; ++i)
             if (job_of[i] >= 0) {
-                s->P0[i] = jobs[job_of[i]].P0;
+                s->P0[i] = 0.5 * (lo[job_of[i]] + hi[job_of[i]]);
                 s->dinst[i].P0 = s->P0[i];
             }
     }
     DevBuffers &b = s->b;
+    {
+        std::vector<int> ci(total);
+        bool one = true;
+        for (int i = 0; i < s->n_inst; ++i) {
+            for (int c = 0; c < nc; ++c) ci[i * nc + c] = i;
+            one = one && s->dinst[i].substeps == 1;
+        }
+        if ((rc = upload(b.cell_inst, ci.data(), ci.size() * sizeof(int), s->stream, "upload cell instances"))) return rc;
+        s->p.ttm_one_substep = one && !s->lat ? 1 : 0;
+    }
     if ((rc = upload(b.Te, Te.data(), total * sizeof(double), s->stream, "upload T_e"))) return rc;
     if ((rc = upload(b.Tl, Te.data(), total * sizeof(double), s->stream, "upload T_l"))) return rc;
     if ((rc = upload(b.src_shape, shape.data(), total * sizeof(double), s->stream, "upload shape"))) return rc;
@@ -707,6 +832,8 @@ int tts_set_ttm_grid(tts_system *s, const tts_ttm_desc *t)
     TTS_CUDA(cudaStreamSynchronize(s->stream), "set ttm");
     s->tp = tp;
     s->ttm_active = true;
+    s->p.sigma_per_step = s->p.ttm_one_substep ? 0 : 1;
+    if ((rc = refresh_sigma(s))) return rc;
     if (s->lat) {
         // bath cells from the current positions; ion energy tallies per cell
         if ((rc = lattice_ensure_cell_acc(s)) || (rc = lattice_refresh_now(s))) return rc;
@@ -771,8 +898,100 @@ int tts_step(tts_system *s, int64_t nsteps)
         int rc = build_graph(s);
         if (rc) return rc;
     }
-    for (int64_t i = 0; i < nsteps; ++i) TTS_CUDA(cudaGraphLaunch(s->graph, s->stream), "launch step graph");
+    int64_t left = nsteps;
+    for (; left >= s->graph_steps; left -= s->graph_steps)
+        TTS_CUDA(cudaGraphLaunch(s->graph_multi, s->stream), "launch step graph");
+    for (; left > 0; --left) TTS_CUDA(cudaGraphLaunch(s->graph, s->stream), "launch step graph");
     s->launches += nsteps * s->kernels_per_step;
+    return TTS_OK;
+}
+
+int tts_autotune(tts_system *s, int probe_steps, int *chosen, int *n_configs)
+{
+    if (!s || probe_steps < 1) return fail(TTS_ERR_ARG, "bad argument");
+    if (s->profiling) return fail(TTS_ERR_STATE, "switch profiling off before autotuning");
+    const int n = s->eng ? engine_num_configs(s->eng) : static_cast<int>(s->pass_blocks.size());
+    if (n_configs) *n_configs = n;
+    if (n <= 1) {
+        if (chosen) *chosen = 0;
+        return TTS_OK;
+    }
+    // cache key: engine, precision, instance count and every instance's shape
+    std::string key = std::to_string(s->engine) + "/" + std::to_string(s->precision) + "/" +
+                      std::to_string(s->n_inst) + "/" + std::to_string(s->zmax) + "/" + std::to_string(s->lat != nullptr);
+    for (const HostInstance &hi : s->host)
+        key += ":" + std::to_string(hi.cells[0]) + "x" + std::to_string(hi.cells[1]) + "x" + std::to_string(hi.cells[2]);
+    static std::mutex cache_lock;
+    static std::map<std::string, int> cache;
+    int best = -1;
+    {
+        std::lock_guard<std::mutex> g(cache_lock);
+        auto it = cache.find(key);
+        if (it != cache.end()) best = it->second;
+    }
+    if (best < 0) {
+        size_t nbytes = 0;
+        int rc = tts_get_state(s, nullptr, &nbytes);
+        if (rc) return rc;
+        std::vector<char> saved(nbytes);
+        if ((rc = tts_get_state(s, saved.data(), &nbytes))) return rc;
+        const int64_t launches0 = s->launches;
+        cudaEvent_t e0, e1;
+        TTS_CUDA(cudaEventCreate(&e0), "autotune event");
+        TTS_CUDA(cudaEventCreate(&e1), "autotune event");
+        float best_ms = 0.0f;
+        for (int c = 0; c < n && !rc; ++c) {
+            if (s->eng) engine_set_config(s->eng, c);
+            else s->pass_block = s->pass_blocks[c];
+            s->dirty = true;
+            if ((rc = tts_step(s, 2))) break;                       // graph build and warm-up
+            if (cudaEventRecord(e0, s->stream) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "autotune"); break; }
+            if ((rc = tts_step(s, probe_steps))) break;
+            cudaEventRecord(e1, s->stream);
+            cudaError_t ce = cudaEventSynchronize(e1);
+            if (ce != cudaSuccess) { rc = cuda_fail(ce, "autotune"); break; }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (best < 0 || ms < best_ms) {
+                best = c;
+                best_ms = ms;
+            }
+            if ((rc = tts_set_state(s, saved.data(), nbytes))) break;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc) return rc;
+        s->launches = launches0;
+        std::lock_guard<std::mutex> g(cache_lock);
+        cache[key] = best;
+    }
+    if (s->eng) engine_set_config(s->eng, best);
+    else s->pass_block = s->pass_blocks[best];
+    s->dirty = true;
+    if (chosen) *chosen = best;
+    return TTS_OK;
+}
+
+int tts_set_config(tts_system *s, int index, int *current, int *n_configs)
+{
+    if (!s) return fail(TTS_ERR_ARG, "null system");
+    const int n = s->eng ? engine_num_configs(s->eng) : static_cast<int>(s->pass_blocks.size());
+    if (n_configs) *n_configs = n;
+    if (index >= n) return fail(TTS_ERR_ARG, "configuration index out of range");
+    if (index >= 0 && n > 0) {
+        if (s->eng) engine_set_config(s->eng, index);
+        else s->pass_block = s->pass_blocks[index];
+        s->dirty = true;
+    }
+    if (current) {
+        if (s->eng) *current = engine_config(s->eng);
+        else {
+            int c = 0;
+            for (int k = 0; k < n; ++k)
+                if (s->pass_blocks[k] == s->pass_block) c = k;
+            *current = c;
+        }
+    }
     return TTS_OK;
 }
 
@@ -846,13 +1065,28 @@ int tts_observe_now(tts_system *s, int inst, double *out)
     int rc = check_inst(s, inst);
     if (rc) return rc;
     if (!out) return fail(TTS_ERR_ARG, "null output");
+    cudaError_t e = cudaErrorNotSupported;
     if (s->eng) {
-        cudaError_t e = engine_sync_to_general(s->eng, s->b, s->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "engine gather");
+        StepParams p = s->p;
+        p.obs_blocks = s->obs_blocks;
+        e = engine_obs_partials(s->eng, p, s->b, 1, s->stream);
+        if (e == cudaSuccess) {
+            e = launch_obs_reduce(p, s->b, 1, s->stream);
+            s->launches += 2;
+            if (e != cudaSuccess) return cuda_fail(e, "observe");
+        } else if (e != cudaErrorNotSupported) {
+            return cuda_fail(e, "observe");
+        } else {
+            e = engine_sync_to_general(s->eng, s->b, s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "engine gather");
+            e = cudaErrorNotSupported;
+        }
     }
-    cudaError_t e = launch_obs(s->p, s->b, s->precision, s->obs_blocks, 1, s->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "observe");
-    s->launches += 2;
+    if (e == cudaErrorNotSupported) {
+        e = launch_obs(s->p, s->b, s->precision, s->obs_blocks, 1, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "observe");
+        s->launches += 2;
+    }
     TTS_CUDA(cudaStreamSynchronize(s->stream), "observe");
     TTS_CUDA(cudaMemcpy(out, s->b.obs_now + size_t(inst) * TTS_NOBS, TTS_NOBS * sizeof(double), cudaMemcpyDeviceToHost),
              "read observation");
@@ -896,6 +1130,52 @@ int tts_set_all_spins(tts_system *s, const double *xyz)
         if (rc) return rc;
         xyz += 3 * s->dinst[i].n;
     }
+    return TTS_OK;
+}
+
+namespace {
+int io_buffer(tts_system *s)
+{
+    if (s->io_buf) return TTS_OK;
+    cudaError_t e = cudaMalloc(&s->io_buf, size_t(s->n_total) * 3 * s->rsize);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        s->io_buf = nullptr;
+        return fail(TTS_ERR_OOM, "spin I/O staging buffer");
+    }
+    return TTS_OK;
+}
+}  // namespace
+
+int tts_read_spins_async(tts_system *s, void *host, size_t bytes)
+{
+    if (!s || !host) return fail(TTS_ERR_ARG, "null argument");
+    if (bytes != size_t(s->n_total) * 3 * s->rsize) return fail(TTS_ERR_ARG, "byte count is not 3 n_total reals");
+    int rc = io_buffer(s);
+    if (rc) return rc;
+    if (s->eng) {
+        cudaError_t e = engine_sync_to_general(s->eng, s->b, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "engine gather");
+    }
+    TTS_CUDA(launch_spins_to_atoms(s->b, s->n_total, s->n_inst, s->precision, s->io_buf, s->stream), "spin reorder");
+    TTS_CUDA(cudaMemcpyAsync(host, s->io_buf, bytes, cudaMemcpyDeviceToHost, s->stream), "read spins");
+    s->launches += s->eng ? 2 : 1;
+    return TTS_OK;
+}
+
+int tts_write_spins_async(tts_system *s, const void *host, size_t bytes)
+{
+    if (!s || !host) return fail(TTS_ERR_ARG, "null argument");
+    if (bytes != size_t(s->n_total) * 3 * s->rsize) return fail(TTS_ERR_ARG, "byte count is not 3 n_total reals");
+    int rc = io_buffer(s);
+    if (rc) return rc;
+    TTS_CUDA(cudaMemcpyAsync(s->io_buf, host, bytes, cudaMemcpyHostToDevice, s->stream), "write spins");
+    TTS_CUDA(launch_spins_from_atoms(s->b, s->n_total, s->n_inst, s->precision, s->io_buf, s->stream), "spin reorder");
+    if (s->eng) {
+        cudaError_t e = engine_sync_from_general(s->eng, s->b, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "engine scatter");
+    }
+    s->launches += s->eng ? 2 : 1;
     return TTS_OK;
 }
 
@@ -947,7 +1227,7 @@ int tts_set_ttm_state(tts_system *s, int inst, const double *Te, const double *T
     const DevInstance &di = s->dinst[inst];
     if (Te) TTS_CUDA(cudaMemcpy(s->b.Te + di.cell_begin, Te, di.ncells * sizeof(double), cudaMemcpyHostToDevice), "write T_e");
     if (Tl) TTS_CUDA(cudaMemcpy(s->b.Tl + di.cell_begin, Tl, di.ncells * sizeof(double), cudaMemcpyHostToDevice), "write T_l");
-    return TTS_OK;
+    return refresh_sigma(s);
 }
 
 int tts_get_step(tts_system *s, int64_t *step)
@@ -994,7 +1274,7 @@ int tts_get_state(tts_system *s, void *buf, size_t *nbytes)
     const size_t en = s->n_inst * sizeof(double);
     const size_t oc = s->n_inst * sizeof(int64_t);
     const size_t ring = size_t(s->n_inst) * s->obs_capacity * TTS_NOBS * sizeof(double);
-    const size_t need = hdr + spin + cells + en + oc + ring;
+    const size_t need = hdr + spin + cells + en + oc + ring + lattice_state_bytes(s);
     if (!buf) {
         *nbytes = need;
         return TTS_OK;
@@ -1023,6 +1303,9 @@ int tts_get_state(tts_system *s, void *buf, size_t *nbytes)
     TTS_CUDA(cudaMemcpy(o, s->b.obs_count, oc, cudaMemcpyDeviceToHost), "read counts");
     o += oc;
     TTS_CUDA(cudaMemcpy(o, s->b.obs_ring, ring, cudaMemcpyDeviceToHost), "read ring");
+    o += ring;
+    int rc = lattice_state_io(s, o, true);
+    if (rc) return rc;
     *nbytes = need;
     return TTS_OK;
 }
@@ -1056,6 +1339,12 @@ int tts_set_state(tts_system *s, const void *buf, size_t nbytes)
     o += s->n_inst * sizeof(int64_t);
     TTS_CUDA(cudaMemcpy(s->b.obs_ring, o, size_t(s->n_inst) * s->obs_capacity * TTS_NOBS * sizeof(double),
                         cudaMemcpyHostToDevice), "write ring");
+    o += size_t(s->n_inst) * s->obs_capacity * TTS_NOBS * sizeof(double);
+    {
+        int rc = lattice_state_io(s, const_cast<char *>(o), false);
+        if (rc) return rc;
+        if ((rc = refresh_sigma(s))) return rc;
+    }
     if (s->eng) {
         cudaError_t e = engine_sync_from_general(s->eng, s->b, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "engine scatter");

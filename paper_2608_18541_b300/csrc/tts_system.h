@@ -41,6 +41,9 @@ int64_t lattice_units_per_step(const tts_system *s);
 int lattice_refresh_now(tts_system *s);
 int lattice_ensure_cell_acc(tts_system *s);
 double lattice_step_length(const tts_system *s);
+size_t lattice_state_bytes(const tts_system *s);
+int lattice_state_io(tts_system *s, char *buf, bool save);
+int lattice_refresh_tables(tts_system *s);
 
 }  // namespace tts
 
@@ -77,7 +80,9 @@ struct tts_system {
     int obs_capacity = 1024;
     tts::DevBuffers b;
     tts::StepParams p{};
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;        // one step
+    cudaGraphExec_t graph_multi = nullptr;  // graph_steps steps
+    int graph_steps = 16;
     int kernels_per_step = 0;
     int64_t launches = 0;
     bool dirty = true;
@@ -88,5 +93,8 @@ struct tts_system {
     double prof_ms = 0.0;
     int64_t prof_steps = 0;
     tts::LatticeState *lat = nullptr;               // moving lattice, if switched on
+    int pass_block = 256;                           // general engine: threads per pass CTA
+    std::vector<int> pass_blocks = {128, 256, 512}; // general engine: autotuner candidates
+    void *io_buf = nullptr;                         // bulk spin I/O staging, 3 n_total reals
 };
 

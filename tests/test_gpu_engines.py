@@ -185,3 +185,56 @@ def test_full_size_ensemble_1024_resident_fp32():
     picks = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 17, 511, 1023})
     for inst in picks:
         _check_instance(g, sysd, ttm, inst, 20, 32)
+
+
+@pytest.mark.parametrize("engine,sysf", [
+    ("checker", lambda: (W.gdfeco_sc(16), W.ttm_single_cell(1500.0, 20 * FS))),
+    ("resident", lambda: W.config_ensemble(n_peak=1, n_dur=2, n_real=4, lmin=6, lmax=11)),
+    ("general", lambda: (W.bcc_fe(6), None)),
+])
+def test_autotune_keeps_results_bitwise(engine, sysf):
+    sysd, ttm = sysf()
+    a = P.System(sysd, ttm, precision=32, engine=engine)
+    a.step(30)
+    b = P.System(sysd, ttm, precision=32, engine=engine)
+    chosen, n = b.autotune(probe_steps=5)
+    assert n >= 2 and 0 <= chosen < n
+    assert b.get_step() == 0                 # the probes left no trace
+    b.step(30)
+    for i in range(a.n_instances):
+        assert np.array_equal(a.get_spins(i), b.get_spins(i))
+
+
+def _many_small_with_grid():
+    """32 GdFeCo realisations of 16^3 with a 4^3 TTM grid each: more (column,
+    z-plane) work units than the staged pass keeps CTAs, so a CTA marches over
+    several planes and across column boundaries."""
+    sysd = W.gdfeco_sc(16)
+    sysd["instances"] = [{"nx": 16, "ny": 16, "nz": 16, "frac1": 0.25} for _ in range(32)]
+    return sysd, W.ttm_xy_spot(4, 1500.0, sigma_xy=20.0)
+
+
+@pytest.mark.parametrize("sysf", [
+    lambda: (W.gdfeco_sc(16), W.ttm_single_cell(1500.0, 20 * FS)),
+    _many_small_with_grid,
+    lambda: (dict(W.gdfeco_sc(10), nx=16, ny=10, nz=12), W.ttm_single_cell(1200.0, 20 * FS)),
+])
+def test_every_checker_config_gives_the_same_spins(sysf):
+    """The staged (shared-memory) pass and every block shape of the direct
+    pass compute each site with the same arithmetic: bitwise equal spins."""
+    sysd, ttm = sysf()
+    g = P.System(sysd, ttm, precision=32, engine="checker")
+    cur, n = g.set_config(-1)
+    assert n >= 2 and cur == 0
+    state = g.get_state()
+    ref = None
+    for c in range(n):
+        g.set_state(state)
+        assert g.set_config(c)[0] == c
+        g.step(12)
+        spins = [g.get_spins(i) for i in range(g.n_instances)]
+        if ref is None:
+            ref = spins
+        else:
+            for a, b in zip(ref, spins):
+                assert np.array_equal(a, b), c

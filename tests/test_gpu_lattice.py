@@ -77,3 +77,18 @@ def test_full_size_moving_fe_40():
     dx -= np.round(dx / L) * L
     assert np.abs(dx).max() < 2e-4
     assert np.abs(g.get_spins() - o.spins()).max() < 2e-5
+
+
+def test_moving_lattice_checkpoint_resume_is_bitwise():
+    s, t, lat = _case(n=6)
+    a = P.System(s, t, precision=32, lattice=lat)
+    a.step(3)
+    blob = a.get_state()
+    a.step(4)
+    b = P.System(s, t, precision=32, lattice=lat)
+    b.set_state(blob)
+    b.step(4)
+    assert np.array_equal(a.get_spins(), b.get_spins())
+    assert np.array_equal(a.get_positions(), b.get_positions())
+    assert np.array_equal(a.get_velocities(), b.get_velocities())
+    assert np.array_equal(a.get_ttm(0, 16)[0], b.get_ttm(0, 16)[0])
