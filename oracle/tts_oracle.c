@@ -779,11 +779,38 @@ static void spin_sweep(orc_sys *S)
     for (int c = K - 2; c >= 0; --c) colour_pass(S, c, 0.5 * dt, pass++);
 }
 
+/* Merged sweep, one step (K >= 2).  The leading pass of colour 0 is A_0(dt/2)
+ * when the previous step closed, else the bridge A_0(dt) that merges the
+ * previous step's trailing half with this step's leading half; it is centred
+ * on t_n, so it uses this step's bath T_e(t_n), counter (atom, n, pass 0) and
+ * the full-step noise amplitude.  Inner passes as in the symmetric sweep; the
+ * trailing A_0(dt/2) (pass 2K-2) only when the step closes. */
+static void merged_sweep(orc_sys *S, int open, int close)
+{
+    int K = S->ncolours;
+    double dt = S->p.dt;
+    uint32_t pass = 0;
+    colour_pass(S, 0, open ? dt : 0.5 * dt, pass++);
+    for (int c = 1; c < K - 1; ++c) colour_pass(S, c, 0.5 * dt, pass++);
+    colour_pass(S, K - 1, dt, pass++);
+    for (int c = K - 2; c >= 1; --c) colour_pass(S, c, 0.5 * dt, pass++);
+    if (close) colour_pass(S, 0, 0.5 * dt, pass);
+}
+
 void orc_step(orc_sys *S, int64_t nsteps)
 {
     double dt = S->p.dt;
+    int merged = S->p.sweep == 1 && S->ncolours >= 2;
+    int open = 0;
     for (int64_t it = 0; it < nsteps; ++it) {
-        spin_sweep(S);
+        if (merged) {
+            int sample = S->p.sample_every > 0 && (S->step + 1) % S->p.sample_every == 0;
+            int close = sample || it == nsteps - 1;
+            merged_sweep(S, open, close);
+            open = !close;
+        } else {
+            spin_sweep(S);
+        }
         if (S->has_ttm)
             S->src_energy += ttm_advance(S, S->Te, S->Tl, S->step * dt, dt, S->P0, 1);
         S->step++;

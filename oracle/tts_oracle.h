@@ -46,6 +46,7 @@ typedef struct {
     uint32_t instance;      /* realisation / instance id (Philox counter word 3) */
     int sample_every;       /* record observables every this many steps (0 = never) */
     double noise_mu_power;  /* 0.5: FDT noise ~ mu^-1/2; 1: the variant without mu_fdt */
+    int sweep;              /* 0 symmetric sweep per step; 1 merged sweep (see orc_step) */
 } orc_params;
 
 typedef struct {
@@ -101,6 +102,12 @@ void orc_flow(double s[3], const double Bfield[3], double alpha, double h);
 orc_sys *orc_create(const orc_params *p, char *err, int errlen);
 void orc_free(orc_sys *s);
 int orc_set_ttm(orc_sys *s, const orc_ttm *t, char *err, int errlen);
+/* Advance nsteps spin steps.  Symmetric sweep (sweep = 0): every step is
+ * A_0(dt/2) .. A_{K-2}(dt/2) A_{K-1}(dt) A_{K-2}(dt/2) .. A_0(dt/2).  Merged
+ * sweep (sweep = 1, K >= 2): the trailing A_0(dt/2) of a step and the leading
+ * A_0(dt/2) of the next are one pass A_0(dt) centred on the step boundary; the
+ * sweep closes with A_0(dt/2) at every sampling step and at the end of the
+ * call, so observables and the state between calls are at whole steps. */
 void orc_step(orc_sys *s, int64_t nsteps);
 
 int orc_natoms(const orc_sys *s);
