@@ -170,6 +170,31 @@ def ensemble_leg(P, W, stream, steps=200, sample=8):
             "ratio": batched / fp64, "unit": "spin-steps/s"}
 
 
+def merged_leg(P, sysd, ttm, args, stream, spins):
+    """The same workload with the merged (leapfrog) sweep: 2 colour passes a
+    step instead of 3, the sweep closed at every sample (once per chunk).  A
+    different integrator of the same order, reported beside the headline."""
+    import torch
+    g = P.System(dict(sysd, sweep="merged"), ttm, precision=args.precision, engine=args.engine,
+                 stream=stream.cuda_stream)
+    for _ in range(args.warmup):
+        g.step(args.chunk)
+    g.sync()
+    steps = max(1, min(args.steps, 10))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        g.step(args.chunk)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    del g
+    return {"value": spins * steps * args.chunk / (ms / 1e3), "unit": "spin-steps/s",
+            "ms_per_step": ms / steps, "steps": steps, "passes_per_dt": 2,
+            "note": "sweep closed at every sampling step (once per chunk) and at the end of every call"}
+
+
 def cpu_oracle_rate(sysd, ttm, steps):
     """Time the FP64 CPU oracle (single thread) on one realisation."""
     import oracle as O
@@ -227,6 +252,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-merged", action="store_true")
     args = ap.parse_args()
 
     world = _env_int("WORLD_SIZE", 1)
@@ -339,6 +365,10 @@ def main():
                 "traffic": _traffic(kernel_name, args.precision), "kernel": kernel_name,
                 "bytes_per_unit": bpu, "units_per_launch": spins,
                 "avg_launch_ms": kern_ms / max(kern_steps, 1)}
+    engine = g.engine
+    merged = None
+    if world == 1 and not args.no_merged:
+        merged = merged_leg(P, sysd, ttm, args, stream, spins)
     ens = None
     if world == 1 and not args.no_ensemble:
         from paper_2608_18541_b300 import workloads as W
@@ -355,10 +385,10 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
         "config": {"workload": desc, "spins_per_gpu": spins, "dt_per_step": args.chunk,
-                   "engine": g.engine, "l2": "state and tables exceed L2 (126 MB) per step" if spins * 16 > 126e6
+                   "engine": engine, "l2": "state and tables exceed L2 (126 MB) per step" if spins * 16 > 126e6
                    else "working set may fit L2", "parallelism": "instances sharded, dp%d" % world},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-        "clocks": clocks, "ensemble": ens,
+        "clocks": clocks, "ensemble": ens, "merged_sweep": merged,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

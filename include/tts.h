@@ -72,6 +72,18 @@ extern "C" {
 #define TTS_ENGINE_CHECKER 2       /* sc lattice, even edges: implicit stencil, fused passes */
 #define TTS_ENGINE_RESIDENT 3      /* sc lattice: one instance per CTA held in shared memory */
 
+/* Order of the colour passes within and across steps (paper Sec. II.A: the
+ * symmetric Suzuki-Trotter splitting over colour classes). */
+#define TTS_SWEEP_SYMMETRIC 0      /* every step A_0(dt/2)..A_{K-1}(dt)..A_0(dt/2) */
+#define TTS_SWEEP_MERGED 1         /* leapfrog form: the trailing A_0(dt/2) of a step and the
+                                      leading A_0(dt/2) of the next run as one A_0(dt) centred
+                                      on the step boundary (bath and Philox counter of the new
+                                      step); closed with A_0(dt/2) at sampling steps and at the
+                                      end of every tts_step call, so observables and the state
+                                      seen between calls are at whole steps.  2K-2 passes a
+                                      step instead of 2K-1; needs the same colour count K >= 2
+                                      in every instance; not with a moving lattice. */
+
 /* Exchange coupling of one species pair.  The pair energy is -J(r) s_i.s_j. */
 typedef struct {
     int kind;       /* TTS_EXCH_* */
@@ -114,6 +126,7 @@ typedef struct {
     int engine;                  /* TTS_ENGINE_* */
     int instance_base;           /* global id of instance 0 (Philox counter word 3 and
                                     placement stream are keyed by instance_base + index) */
+    int sweep;                   /* TTS_SWEEP_* */
 } tts_system_desc;
 
 #define TTS_SOURCE_NONE 0

@@ -82,6 +82,7 @@ struct CheckerArgs {
     uint32_t nhalf;              // sites per colour
     int64_t n_inst_sites;        // sites per instance
     uint32_t inst_base;          // global id of instance 0
+    SweepCtl sw;                 // merged sweep: leading / trailing colour-0 pass
 };
 
 // One colour pass, one site per thread.  Block (BX, BY) threads cover BX
@@ -94,6 +95,11 @@ template <typename R, bool AXZ>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) checker_pass_kernel(CheckerArgs<R> a, int colour, int hsel, int pass)
 {
     using V = typename Vec4<R>::T;
+    {
+        int hd = -1;
+        if (a.sw.mode != 0 && !sweep_gate(a.sw, a.step, hd)) return;
+        if (hd >= 0) hsel = hd;
+    }
     // block index -> (row block, x block); the quotient is uniform over the block
     const uint32_t yb = blockIdx.x / a.nkx;
     const uint32_t kx = (blockIdx.x - yb * a.nkx) * blockDim.x + threadIdx.x;
@@ -175,7 +181,7 @@ struct PairArgs {
     const int64_t *step;
     unsigned int *health;
     PairConsts k;
-    uint32_t key0, key1;
+    PhiloxRoundKeys rk;
     uint32_t Lx, Ly, Lz, hx, Ly2;
     uint32_t nkx;                // blocks along the hx colour sites of a row
     uint32_t nhalf;              // sites per colour
@@ -190,6 +196,8 @@ struct PairArgs {
     int cell0, cstride;
     uint32_t ncx, ncy, ncz;
     FastDiv dLx, dLy, dLz;
+    int shx, shy, shz;           // >= 0: L_k / n_k = 2^sh, c_k = k >> sh
+    SweepCtl sw;                 // merged sweep: leading / trailing colour-0 pass
 };
 
 struct Pair4 {
@@ -246,7 +254,7 @@ __device__ __forceinline__ void site_noise(const PairArgs &a, const PairSite &p,
     const uint32_t atomA = (p.z * a.Ly + p.y2) * a.Lx + 2 * p.kx + p.parA;
     const uint32_t atomB = (p.z * a.Ly + p.y2 + a.Ly2) * a.Lx + 2 * p.kx + p.parB;
     pair_noise(u32x4{atomA, step, static_cast<uint32_t>(pass), ig}, u32x4{atomB, step, static_cast<uint32_t>(pass), ig},
-               a.key0, a.key1, a.k, g1, g2, g3);
+               a.rk, a.k, g1, g2, g3);
 }
 
 // Neighbour sums of a pair from one z plane's tile of the other colour (rows
@@ -290,9 +298,10 @@ __device__ __forceinline__ void neighbour_sums(const PairSite &p, uint32_t hx, u
 // Update the pair from its neighbour sums and own words and store it at pair
 // q of the own colour's planes.
 template <bool AXZ>
-__device__ __forceinline__ void pair_finish(const PairArgs &a, const PairSite &p, int colour, int hsel, f2 g1, f2 g2,
-                                            f2 g3, f2 htx, f2 hty, f2 htz, f2 h1x, f2 h1y, f2 h1z, ulonglong2 olo,
-                                            ulonglong2 ohi, ulonglong2 *Wlo, ulonglong2 *Whi, uint32_t q)
+__device__ __forceinline__ void pair_finish(const PairArgs &a, const PairSite &p, int colour, int hsel, bool h2, f2 g1,
+                                            f2 g2, f2 g3, f2 htx, f2 hty, f2 htz, f2 h1x, f2 h1y, f2 h1z,
+                                            ulonglong2 olo, ulonglong2 ohi, ulonglong2 *Wlo, ulonglong2 *Whi,
+                                            uint32_t q)
 {
     f2 sx{olo.x}, sy{olo.y}, sz{ohi.x};
     const f2 w{ohi.y};
@@ -303,10 +312,13 @@ __device__ __forceinline__ void pair_finish(const PairArgs &a, const PairSite &p
         const int tA = wA != 0.0f ? 1 : 0, tB = wB != 0.0f ? 1 : 0;
         int cA, cB;
         if (a.cell_formula) {
-            const uint32_t cz = fast_div(p.z * a.ncz, a.dLz);
-            const uint32_t cyA = fast_div(p.y2 * a.ncy, a.dLy), cyB = fast_div((p.y2 + a.Ly2) * a.ncy, a.dLy);
-            const uint32_t cxA = fast_div((2 * p.kx + p.parA) * a.ncx, a.dLx);
-            const uint32_t cxB = fast_div((2 * p.kx + p.parB) * a.ncx, a.dLx);
+            auto cc = [](uint32_t v, uint32_t n, const FastDiv &d, int sh) {
+                return sh >= 0 ? v >> sh : fast_div(v * n, d);
+            };
+            const uint32_t cz = cc(p.z, a.ncz, a.dLz, a.shz);
+            const uint32_t cyA = cc(p.y2, a.ncy, a.dLy, a.shy), cyB = cc(p.y2 + a.Ly2, a.ncy, a.dLy, a.shy);
+            const uint32_t cxA = cc(2 * p.kx + p.parA, a.ncx, a.dLx, a.shx);
+            const uint32_t cxB = cc(2 * p.kx + p.parB, a.ncx, a.dLx, a.shx);
             const int base = a.cell0 + p.inst * a.cstride;
             cA = base + int((cz * a.ncy + cyA) * a.ncx + cxA);
             cB = base + int((cz * a.ncy + cyB) * a.ncx + cxB);
@@ -320,7 +332,7 @@ __device__ __forceinline__ void pair_finish(const PairArgs &a, const PairSite &p
         }
         sig = f2_make(a.sigma[(cA * TTS_MAX_SPECIES + tA) * 2 + hsel], a.sigma[(cB * TTS_MAX_SPECIES + tB) * 2 + hsel]);
     }
-    pair_update<AXZ>(sx, sy, sz, htx, hty, htz, h1x, h1y, h1z, w, a.noise != 0, sig, g1, g2, g3, a.k);
+    pair_update<AXZ>(sx, sy, sz, htx, hty, htz, h1x, h1y, h1z, w, a.noise != 0, sig, g1, g2, g3, a.k, h2);
     float sA, sB;
     f2_split(sx + sy + sz, sA, sB);
     // a non-finite component makes the sum non-finite
@@ -337,6 +349,10 @@ __device__ __forceinline__ void pair_finish(const PairArgs &a, const PairSite &p
 template <bool AXZ>
 __global__ void __launch_bounds__(256, 4) checker_pair_kernel(PairArgs a, int colour, int hsel, int pass)
 {
+    int hd = -1;
+    if (a.sw.mode != 0 && !sweep_gate(a.sw, a.step, hd)) return;
+    const bool h2 = hd == 1;          // constants made for dt/2, the bridge runs dt
+    if (hd >= 0) hsel = hd;
     const uint32_t yb = blockIdx.x / a.nkx;
     const uint32_t kx = (blockIdx.x - yb * a.nkx) * blockDim.x + threadIdx.x;
     const uint32_t y2 = yb * blockDim.y + threadIdx.y;
@@ -359,7 +375,7 @@ __global__ void __launch_bounds__(256, 4) checker_pair_kernel(PairArgs a, int co
     neighbour_sums(p, hx, Ly2, Olo, Ohi, Olo, Ohi, Olo, Ohi, (zp * Ly2 + y2) * hx, (zm * Ly2 + y2) * hx, r0,
                    (z * Ly2 + yp) * hx, (z * Ly2 + ym) * hx, htx, hty, htz, h1x, h1y, h1z);
     const uint32_t q = r0 + kx;
-    pair_finish<AXZ>(a, p, colour, hsel, g1, g2, g3, htx, hty, htz, h1x, h1y, h1z, Wlo[q], Whi[q], Wlo, Whi, q);
+    pair_finish<AXZ>(a, p, colour, hsel, h2, g1, g2, g3, htx, hty, htz, h1x, h1y, h1z, Wlo[q], Whi[q], Wlo, Whi, q);
 }
 
 // ---------------------------------------------------------------------------
@@ -387,6 +403,10 @@ template <bool AXZ>
 __global__ void __launch_bounds__(256, 3) checker_pair_tiled_kernel(PairArgs a, TileArgs t, int colour, int hsel,
                                                                     int pass)
 {
+    int hd = -1;
+    if (a.sw.mode != 0 && !sweep_gate(a.sw, a.step, hd)) return;
+    const bool h2 = hd == 1;
+    if (hd >= 0) hsel = hd;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_abort;
     const uint32_t hx = a.hx, by = t.by, Ly2 = a.Ly2, Lz = a.Lz;
@@ -488,8 +508,8 @@ __global__ void __launch_bounds__(256, 3) checker_pair_tiled_kernel(PairArgs a, 
                                ty * hx, htx, hty, htz, h1x, h1y, h1z);
                 const uint32_t qs = ty * hx + tx;
                 const uint32_t q = (z * Ly2 + y0 + ty) * hx + tx;
-                pair_finish<AXZ>(a, p, colour, hsel, g1, g2, g3, htx, hty, htz, h1x, h1y, h1z, Tw[qs], Tw[tw + qs],
-                                 gw, gw + a.npair, q);
+                pair_finish<AXZ>(a, p, colour, hsel, h2, g1, g2, g3, htx, hty, htz, h1x, h1y, h1z, Tw[qs],
+                                 Tw[tw + qs], gw, gw + a.npair, q);
             }
             ++c_o;
             ++c_w;
@@ -717,6 +737,7 @@ struct ResArgs {
     int obs_capacity;
     int nmax;                            // shared-memory capacity in sites
     int ttm_active;
+    int merged;                          // merged (leapfrog) sweep
     TtmParams tp;
 };
 
@@ -890,6 +911,9 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<R> a, int64_t 
         }
         __syncthreads();
         const int Lx = I.L[0], Ly = I.L[1], Lz = I.L[2];
+        // merged sweep: colour 0 left half a step ahead by the previous step
+        const bool mer = a.merged && I.ncolours >= 2;
+        bool open = false;
         for (int64_t st = 0; st < nsteps; ++st) {
             const int64_t step = step0 + st;
             if (threadIdx.x == 0) {
@@ -898,9 +922,12 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<R> a, int64_t 
             }
             __syncthreads();
             const int K = I.ncolours;
+            const bool close =
+                !mer || st == nsteps - 1 || (a.sample_every > 0 && (step + 1) % a.sample_every == 0);
             for (int p = 0; p < 2 * K - 1; ++p) {
+                if (mer && p == 2 * K - 2 && !close) continue;     // the trailing half waits for the bridge
                 const int c = p < K - 1 ? p : (p == K - 1 ? K - 1 : 2 * K - 2 - p);
-                const int hsel = p == K - 1 ? 1 : 0;
+                const int hsel = (p == K - 1 || (mer && p == 0 && open)) ? 1 : 0;
                 const R h = hsel ? R(a.dt) : R(0.5 * a.dt);
                 const int beg = I.colour_begin[c], end = I.colour_begin[c + 1];
                 for (int idx = beg + threadIdx.x; idx < end; idx += blockDim.x) {
@@ -945,6 +972,7 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<R> a, int64_t 
                 }
                 __syncthreads();
             }
+            open = mer && !close;
             // one-cell TTM, t_n -> t_n+1 (no diffusion on a single cell)
             if (threadIdx.x == 0 && a.ttm_active) {
                 double T[2] = {Te, Tl};
@@ -1483,8 +1511,7 @@ PairArgs pair_args(const EngineState *e, const StepParams &p, const DevBuffers &
     a.step = b.step;
     a.health = b.health;
     a.k = make_pair_consts(e, p, hsel);
-    a.key0 = p.key0;
-    a.key1 = p.key1;
+    a.rk = philox_round_keys(p.key0, p.key1);
     a.Lx = e->shape[0];
     a.Ly = e->shape[1];
     a.Lz = e->shape[2];
@@ -1505,6 +1532,19 @@ PairArgs pair_args(const EngineState *e, const StepParams &p, const DevBuffers &
     a.dLx = make_fastdiv(e->shape[0]);
     a.dLy = make_fastdiv(e->shape[1]);
     a.dLz = make_fastdiv(e->shape[2]);
+    int *sh[3] = {&a.shx, &a.shy, &a.shz};
+    for (int k = 0; k < 3; ++k) {
+        *sh[k] = -1;
+        const uint32_t L = e->shape[k], n = e->ncell[k];
+        if (n > 0 && L % n == 0) {
+            const uint32_t q = L / n;
+            if ((q & (q - 1)) == 0) {
+                int b = 0;
+                while ((1u << b) < q) ++b;
+                *sh[k] = b;
+            }
+        }
+    }
     return a;
 }
 
@@ -1549,6 +1589,16 @@ cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuf
     }
     if (err == cudaSuccess && ev0) err = cudaEventRecord(ev0, st);
     const int npass = 2 * e->K - 1;
+    // merged sweep: the first pass leads (dt/2 or a dt bridge), the last trails
+    auto ctl = [&](int pass) {
+        SweepCtl w;
+        if (!p.merged) return w;
+        w.mode = pass == 0 ? 1 : (pass == npass - 1 ? 2 : 0);
+        w.open = b.open;
+        w.target = b.target;
+        w.sample_every = p.sample_every;
+        return w;
+    };
     for (int pass = 0; pass < npass && err == cudaSuccess; ++pass) {
         const int c = pass < e->K - 1 ? pass : (pass == e->K - 1 ? e->K - 1 : 2 * e->K - 2 - pass);
         const int hsel = pass == e->K - 1 ? 1 : 0;
@@ -1569,6 +1619,7 @@ cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuf
             CheckerArgs<double> a{};
             a.S = static_cast<double4a *>(e->S);
             fill_shape(a);
+            a.sw = ctl(pass);
             a.cell = b.cell;
             a.sigma = static_cast<const double *>(b.sigma);
             a.step = b.step;
@@ -1584,7 +1635,8 @@ cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuf
             else
                 checker_pass_kernel<double, false><<<grid, block, 0, st>>>(a, c, hsel, pass);
         } else {
-            const PairArgs a = pair_args(e, p, b, hsel);
+            PairArgs a = pair_args(e, p, b, hsel);
+            a.sw = ctl(pass);
             if (e->bx == 0) {
                 if (e->axis_z)
                     checker_pair_tiled_kernel<true><<<e->tile_grid, 256, e->tile_smem, st>>>(a, e->tile, c, hsel, pass);
@@ -1660,6 +1712,7 @@ cudaError_t engine_run_steps(EngineState *e, const StepParams &p, const DevBuffe
         a.obs_capacity = p.obs_capacity;
         a.nmax = e->nmax;
         a.ttm_active = ttm_active ? 1 : 0;
+        a.merged = p.merged;
         a.tp = tp;
     };
     if (err == cudaSuccess) {

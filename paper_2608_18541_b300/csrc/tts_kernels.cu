@@ -153,8 +153,10 @@ __device__ __forceinline__ void det_field(const StepParams &p, int64_t slot, int
 template <typename R>
 __global__ void __launch_bounds__(512) pass_general_kernel(StepParams p, DevBuffers b, int pass,
                                                            const PassRange *__restrict__ ranges, int nranges,
-                                                           int64_t nwork)
+                                                           int64_t nwork, SweepCtl sw)
 {
+    int hsel_dyn = -1;
+    if (sw.mode != 0 && !sweep_gate(sw, b.step, hsel_dyn)) return;
     const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (gid >= nwork) return;
     int lo = 0, hi = nranges - 1;
@@ -169,8 +171,9 @@ __global__ void __launch_bounds__(512) pass_general_kernel(StepParams p, DevBuff
     R sx = S0[slot], sy = S1[slot], sz = S2[slot];
     R Bx, By, Bz;
     det_field<R>(p, slot, t, sx, sy, sz, S0, S1, S2, b.nbr, static_cast<const R *>(b.nbr_w), Bx, By, Bz);
-    const R h = r.hsel ? R(p.dt) : R(0.5 * p.dt);
-    const R sig = static_cast<const R *>(b.sigma)[(int64_t(b.cell[slot]) * TTS_MAX_SPECIES + t) * 2 + r.hsel];
+    const int hsel = hsel_dyn >= 0 ? hsel_dyn : r.hsel;
+    const R h = hsel ? R(p.dt) : R(0.5 * p.dt);
+    const R sig = static_cast<const R *>(b.sigma)[(int64_t(b.cell[slot]) * TTS_MAX_SPECIES + t) * 2 + hsel];
     if (sig > R(0)) {
         const int64_t step = *b.step;
         u32x4 c{static_cast<uint32_t>(b.atom[slot]), static_cast<uint32_t>(step), static_cast<uint32_t>(pass),
@@ -561,15 +564,26 @@ cudaError_t launch_sigma(const StepParams &p, const DevBuffers &b, int ncells, i
 }
 
 cudaError_t launch_pass_general(const StepParams &p, const DevBuffers &b, int precision, int pass,
-                                int64_t range_offset, int nranges, int64_t nwork, cudaStream_t st, int block)
+                                int64_t range_offset, int nranges, int64_t nwork, cudaStream_t st, int block,
+                                SweepCtl sw)
 {
     if (nwork <= 0) return cudaSuccess;
     const int bs = block;
     const int64_t gs = (nwork + bs - 1) / bs;
     if (precision == 64)
-        pass_general_kernel<double><<<gs, bs, 0, st>>>(p, b, pass, b.ranges + range_offset, nranges, nwork);
+        pass_general_kernel<double><<<gs, bs, 0, st>>>(p, b, pass, b.ranges + range_offset, nranges, nwork, sw);
     else
-        pass_general_kernel<float><<<gs, bs, 0, st>>>(p, b, pass, b.ranges + range_offset, nranges, nwork);
+        pass_general_kernel<float><<<gs, bs, 0, st>>>(p, b, pass, b.ranges + range_offset, nranges, nwork, sw);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void set_target_kernel(const int64_t *step, int64_t *target, int64_t n) { *target = *step + n; }
+}  // namespace
+
+cudaError_t launch_set_target(const DevBuffers &b, int64_t n, cudaStream_t st)
+{
+    set_target_kernel<<<1, 1, 0, st>>>(b.step, b.target, n);
     return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@ struct StepParams {
     int ttm_one_substep;     // every TTM grid advances in one sub-step per step
     int sigma_per_step;      // the noise table is rebuilt by its own kernel every step
     int lattice_on;          // observables of a moving lattice (sampled per lattice step)
+    int merged;              // merged (leapfrog) sweep (engines read it from here)
     int64_t *lstep;          // lattice step counter (moving lattice)
     double *lat_partial;     // per observable block: kinetic and pair energy (moving lattice)
 };
@@ -45,6 +46,8 @@ struct DevBuffers {
     DevInstance *inst = nullptr;  // per instance
     PassRange *ranges = nullptr;  // concatenated over passes
     int64_t *step = nullptr;      // device step counter
+    int *open = nullptr;          // merged sweep: colour 0 is half a step ahead
+    int64_t *target = nullptr;    // merged sweep: step count at the end of the current call
     unsigned int *health = nullptr;
     double *obs_partial = nullptr;// per observable block, kObsFields doubles
     int *obs_block_inst = nullptr;// instance of each observable block
@@ -54,6 +57,39 @@ struct DevBuffers {
     double *obs_now = nullptr;    // n_instances * TTS_NOBS
     int *cell_inst = nullptr;     // instance of each TTM cell
 };
+
+// Merged-sweep control of a colour-0 pass (the splitting of paper Sec. II.A in
+// leapfrog form).  mode 0: h fixed by the launch; 1: the leading pass, h = dt
+// (a bridge) when the previous step left colour 0 open, else dt/2; 2: the
+// trailing half-pass, run only when the step closes -- a sampling step or the
+// last step of the call -- and recording for the next step whether it did.
+struct SweepCtl {
+    int mode = 0;
+    int *open = nullptr;
+    const int64_t *target = nullptr;
+    int sample_every = 0;
+};
+
+#ifdef __CUDACC__
+// Apply the control: returns false when the (trailing) pass is skipped;
+// sets hsel for a leading pass.  Every thread of the launch gets the same
+// answer; block 0's thread 0 records the open state.
+__device__ __forceinline__ bool sweep_gate(const SweepCtl &w, const int64_t *step, int &hsel)
+{
+    if (w.mode == 1) {
+        hsel = *w.open ? 1 : 0;
+        return true;
+    }
+    if (w.mode == 2) {
+        const int64_t n = *step;
+        const bool close = (w.sample_every > 0 && (n + 1) % w.sample_every == 0) || n + 1 == *w.target;
+        if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+            *w.open = close ? 0 : 1;
+        return close;
+    }
+    return true;
+}
+#endif
 
 constexpr int kObsFields = 24;       // per species: 12 partial sums
 constexpr int kObsBlock = 128;       // threads of an observable block
@@ -97,7 +133,10 @@ enum HealthBits : unsigned int {
 cudaError_t launch_sigma(const StepParams &p, const DevBuffers &b, int ncells_total, int precision,
                          cudaStream_t st);
 cudaError_t launch_pass_general(const StepParams &p, const DevBuffers &b, int precision, int pass,
-                                int64_t range_offset, int nranges, int64_t nwork, cudaStream_t st, int block = 256);
+                                int64_t range_offset, int nranges, int64_t nwork, cudaStream_t st, int block = 256,
+                                SweepCtl sw = SweepCtl());
+// target = step + n (merged sweep: the call's last step closes)
+cudaError_t launch_set_target(const DevBuffers &b, int64_t n, cudaStream_t st);
 // TTM advance of every instance; with one sub-step per step the grid-parallel
 // path also refreshes the noise table for the next step and, with inc_step,
 // advances the step counter.

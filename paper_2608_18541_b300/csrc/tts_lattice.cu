@@ -622,6 +622,7 @@ int tts_set_lattice(tts_system *s, const tts_lattice_desc *d)
     if (s->ttm_active) return fail(TTS_ERR_STATE, "switch the moving lattice on before setting the TTM grid");
     if (s->desc.lattice == TTS_LATTICE_CLUSTER) return fail(TTS_ERR_UNSUPPORTED, "clusters have no lattice to move");
     if (s->eng) return fail(TTS_ERR_UNSUPPORTED, "a moving lattice runs on the general engine (engine = general)");
+    if (s->merged) return fail(TTS_ERR_UNSUPPORTED, "the merged sweep is for rigid lattices");
     if (d->spin_substeps < 2 || d->spin_substeps % 2) return fail(TTS_ERR_ARG, "spin_substeps must be even and >= 2");
     if (!(d->mass_amu > 0.0) || !(d->morse_rc > 0.0) || !(d->morse_alpha > 0.0) || !(d->skin >= 0.0) ||
         !(d->T_init >= 0.0) || !(d->gamma_p >= 0.0))

@@ -136,11 +136,11 @@ struct PairConsts {
 // Thermal-field directions of two sites: one Philox4x32-10 block per site,
 // Box-Muller to (g1, g2, g3) = -(r01 cos a1, r01 sin a1, r23 cos a3) with
 // r = sqrt(-2 ln u) and a = 2 pi u - pi (so that -cos a = cos 2 pi u).
-__device__ __forceinline__ void pair_noise(const u32x4 &ctrA, const u32x4 &ctrB, uint32_t key0, uint32_t key1,
+__device__ __forceinline__ void pair_noise(const u32x4 &ctrA, const u32x4 &ctrB, const PhiloxRoundKeys &rk,
                                            const PairConsts &k, f2 &g1, f2 &g2, f2 &g3)
 {
-    const u32x4 rA = philox4x32_10(ctrA, key0, key1);
-    const u32x4 rB = philox4x32_10(ctrB, key0, key1);
+    const u32x4 rA = philox4x32_10(ctrA, rk);
+    const u32x4 rB = philox4x32_10(ctrB, rk);
     const f2 u0 = fma2(f2_make(float(rA.x >> 9), float(rB.x >> 9)), k.u_scale, k.u_off);
     const f2 u1 = fma2(f2_make(float(rA.y >> 9), float(rB.y >> 9)), k.u_scale, k.u_off);
     const f2 u2 = fma2(f2_make(float(rA.z >> 9), float(rB.z >> 9)), k.u_scale, k.u_off);
@@ -167,16 +167,23 @@ __device__ __forceinline__ void pair_noise(const u32x4 &ctrA, const u32x4 &ctrB,
 // of all / species-1 neighbour spins, w the species flags; with noise, the
 // thermal field sig * g (a lane with sig = 0 adds nothing).  Returns the new
 // spins.
+// h2: the pass runs for twice the step the constants were made for (the
+// step-length terms gamma' h and kappa gamma' h / 2 doubled, which is exact).
 template <bool AXZ>
 __device__ __forceinline__ void pair_update(f2 &sx, f2 &sy, f2 &sz, f2 htx, f2 hty, f2 htz, f2 h1x, f2 h1y, f2 h1z,
-                                            f2 w, bool noise, f2 sig, f2 g1, f2 g2, f2 g3, const PairConsts &k)
+                                            f2 w, bool noise, f2 sig, f2 g1, f2 g2, f2 g3, const PairConsts &k,
+                                            bool h2)
 {
     const f2 J0 = fma2(w, k.J0d, k.J0c);
     const f2 dJ = fma2(w, k.dJd, k.dJc);
     const f2 kap = fma2(w, k.kd, k.kc);
     const f2 al = fma2(w, k.ald, k.alc);
-    const f2 khg = fma2(w, k.khgd, k.khgc);
-    const f2 gh = fma2(w, k.ghd, k.ghc);
+    f2 khg = fma2(w, k.khgd, k.khgc);
+    f2 gh = fma2(w, k.ghd, k.ghc);
+    if (h2) {
+        khg = khg + khg;
+        gh = gh + gh;
+    }
     const f2 nal = fma2(w, k.nald, k.nalc);
     const f2 cn0 = AXZ ? sz : fma2(sz, k.nz, fma2(sy, k.ny, sx * k.nx));
     const f2 ka = kap * cn0;

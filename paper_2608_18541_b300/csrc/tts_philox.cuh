@@ -80,6 +80,39 @@ TTS_HD u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1)
     return c;
 }
 
+// The ten round keys (k0 + r W_A, k1 + r W_B), r = 0..9, of a key pair: a
+// kernel that receives them as launch parameters XORs constants instead of
+// advancing the key in every round.
+struct PhiloxRoundKeys {
+    uint32_t k0[10], k1[10];
+};
+
+inline PhiloxRoundKeys philox_round_keys(uint32_t k0, uint32_t k1)
+{
+    PhiloxRoundKeys K;
+    for (int r = 0; r < 10; ++r) {
+        K.k0[r] = k0;
+        K.k1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return K;
+}
+
+TTS_HD u32x4 philox4x32_10(u32x4 c, const PhiloxRoundKeys &K)
+{
+    constexpr uint32_t kMulA = 0xD2511F53u;
+    constexpr uint32_t kMulB = 0xCD9E8D57u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hA, lA, hB, lB;
+        mul_hi_lo(kMulA, c.x, hA, lA);
+        mul_hi_lo(kMulB, c.z, hB, lB);
+        c = u32x4{hB ^ c.y ^ K.k0[r], lB, hA ^ c.w ^ K.k1[r], lA};
+    }
+    return c;
+}
+
 // Uniform on (0, 1): the top 23 bits plus one half-bit, (2k + 1) * 2^-24, an
 // exact float as well as an exact double.
 TTS_HD float uniform_f(uint32_t x)

@@ -55,7 +55,7 @@ void free_buffers(tts_system *s)
     void *ptrs[] = {b.sx, b.sy, b.sz, b.atom, b.species, b.cell, b.nbr, b.nbr_w, b.sigma, b.Te, b.Tl,
                     b.src_shape, b.ttm_scratch, b.src_energy, b.inst, b.ranges, b.step, b.health,
                     b.obs_partial, b.obs_block_inst, b.obs_block_begin, b.obs_ring, b.obs_count, b.obs_now,
-                    b.cell_inst};
+                    b.cell_inst, b.open, b.target};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     s->b = DevBuffers{};
@@ -90,6 +90,7 @@ int validate(const tts_system_desc &d)
     if (d.engine < 0 || d.engine > 3) return fail(TTS_ERR_ARG, "unknown engine");
     if (d.sample_every < 0) return fail(TTS_ERR_ARG, "sample_every must be >= 0");
     if (d.instance_base < 0) return fail(TTS_ERR_ARG, "instance_base must be >= 0");
+    if (d.sweep != TTS_SWEEP_SYMMETRIC && d.sweep != TTS_SWEEP_MERGED) return fail(TTS_ERR_ARG, "unknown sweep");
     return TTS_OK;
 }
 
@@ -220,11 +221,28 @@ int alloc_cells(tts_system *s, int ncells_total)
 
 // Issue the kernels of one step on stream c.  ev0 / ev1 (may be null) are
 // recorded around the dominant kernels (the colour passes).
+// Merged-sweep control of pass `pass` of `npass`: the first pass leads, the
+// last trails; every other pass (and every pass of a symmetric sweep) is fixed.
+SweepCtl sweep_ctl(const tts_system *s, int pass, int npass)
+{
+    SweepCtl w;
+    if (!s->merged) return w;
+    w.mode = pass == 0 ? 1 : (pass == npass - 1 ? 2 : 0);
+    w.open = s->b.open;
+    w.target = s->b.target;
+    w.sample_every = s->p.sample_every;
+    return w;
+}
+
 cudaError_t record_step(tts_system *s, cudaStream_t c, int *kernels, cudaEvent_t ev0, cudaEvent_t ev1)
 {
     *kernels = 0;
     if (s->lat) return lattice_record_step(s, c, kernels, ev0, ev1);
-    if (s->eng) return engine_record_step(s->eng, s->p, s->b, s->tp, s->ttm_active, c, kernels, ev0, ev1);
+    if (s->eng) {
+        StepParams p = s->p;
+        p.merged = s->merged ? 1 : 0;
+        return engine_record_step(s->eng, p, s->b, s->tp, s->ttm_active, c, kernels, ev0, ev1);
+    }
     // general engine
     cudaError_t e = cudaSuccess;
     if (s->p.sigma_per_step) {
@@ -235,7 +253,8 @@ cudaError_t record_step(tts_system *s, cudaStream_t c, int *kernels, cudaEvent_t
     for (int pass = 0; pass < s->max_passes && e == cudaSuccess; ++pass) {
         const int64_t off = s->pass_offset[pass];
         const int nr = static_cast<int>(s->pass_offset[pass + 1] - off);
-        e = launch_pass_general(s->p, s->b, s->precision, pass, off, nr, s->pass_work[pass], c, s->pass_block);
+        e = launch_pass_general(s->p, s->b, s->precision, pass, off, nr, s->pass_work[pass], c, s->pass_block,
+                                sweep_ctl(s, pass, s->max_passes));
         ++*kernels;
     }
     if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, c);
@@ -497,6 +516,14 @@ int tts_create_system(const tts_system_desc *desc, void *stream, tts_system **ou
     s->obs_blocks = obs_block;
     s->max_passes = 2 * s->max_colours - 1;
     if (s->n_total > 0x7fffffffLL) return fail(TTS_ERR_UNSUPPORTED, "more than 2^31 atoms in one system");
+    s->merged = false;
+    if (s->desc.sweep == TTS_SWEEP_MERGED) {
+        // one colour: nothing to merge (the step is a single pass)
+        bool same = true;
+        for (const HostInstance &hi : s->host) same = same && hi.ncolours == s->host[0].ncolours;
+        s->merged = s->max_colours >= 2;
+        s->merged_uniform = same;
+    }
 
     // pass ranges: pass p of an instance with K colours takes colour p for
     // p < K-1 (h = dt/2), colour K-1 for p = K-1 (h = dt), colour 2K-2-p after
@@ -575,6 +602,8 @@ int tts_create_system(const tts_system_desc *desc, void *stream, tts_system **ou
     if ((rc = dev_alloc(&b.inst, s->n_inst, "instance table"))) return rc;
     if ((rc = dev_alloc(&b.ranges, s->ranges.size(), "pass ranges"))) return rc;
     if ((rc = dev_alloc(&b.step, 1, "step counter"))) return rc;
+    if ((rc = dev_alloc(&b.open, 1, "sweep state"))) return rc;
+    if ((rc = dev_alloc(&b.target, 1, "sweep target"))) return rc;
     if ((rc = dev_alloc(&b.health, 1, "health word"))) return rc;
     if ((rc = dev_alloc(&b.src_energy, s->n_inst, "source energy"))) return rc;
     if ((rc = dev_alloc(&b.obs_partial, size_t(s->obs_blocks) * kObsFields, "observable partials"))) return rc;
@@ -618,6 +647,8 @@ int tts_create_system(const tts_system_desc *desc, void *stream, tts_system **ou
     if ((rc = upload(b.inst, s->dinst.data(), s->dinst.size() * sizeof(DevInstance), s->stream, "upload instances"))) return rc;
     if ((rc = upload(b.ranges, s->ranges.data(), s->ranges.size() * sizeof(PassRange), s->stream, "upload ranges"))) return rc;
     TTS_CUDA(cudaMemsetAsync(b.step, 0, sizeof(int64_t), s->stream), "zero step");
+    TTS_CUDA(cudaMemsetAsync(b.open, 0, sizeof(int), s->stream), "zero sweep state");
+    TTS_CUDA(cudaMemsetAsync(b.target, 0, sizeof(int64_t), s->stream), "zero sweep target");
     TTS_CUDA(cudaMemsetAsync(b.health, 0, sizeof(unsigned), s->stream), "zero health");
     TTS_CUDA(cudaMemsetAsync(b.src_energy, 0, s->n_inst * sizeof(double), s->stream), "zero energy");
     TTS_CUDA(cudaMemsetAsync(b.obs_count, 0, s->n_inst * sizeof(int64_t), s->stream), "zero obs");
@@ -863,6 +894,13 @@ int tts_step(tts_system *s, int64_t nsteps)
     if (!s) return fail(TTS_ERR_ARG, "null system");
     if (nsteps < 0) return fail(TTS_ERR_ARG, "nsteps must be >= 0");
     if (nsteps == 0) return TTS_OK;
+    if (s->merged && !s->eng && !s->merged_uniform)
+        return fail(TTS_ERR_UNSUPPORTED, "the merged sweep on the general engine needs the same colour count in every instance");
+    if (s->merged && !(s->eng && engine_multi_step(s->eng))) {
+        // the last step of this call closes the merged sweep
+        TTS_CUDA(launch_set_target(s->b, nsteps, s->stream), "sweep target");
+        s->launches += 1;
+    }
     if (s->eng && engine_multi_step(s->eng)) {
         cudaEvent_t ev[2] = {nullptr, nullptr};
         if (s->profiling) {
@@ -873,7 +911,9 @@ int tts_step(tts_system *s, int64_t nsteps)
             s->prof_pair_steps.push_back(nsteps);
         }
         int kernels = 0;
-        cudaError_t e = engine_run_steps(s->eng, s->p, s->b, s->tp, s->ttm_active, nsteps, s->stream, &kernels,
+        StepParams p = s->p;
+        p.merged = s->merged ? 1 : 0;
+        cudaError_t e = engine_run_steps(s->eng, p, s->b, s->tp, s->ttm_active, nsteps, s->stream, &kernels,
                                          ev[0], ev[1]);
         if (e != cudaSuccess) return cuda_fail(e, "resident steps");
         s->launches += kernels;
@@ -1243,6 +1283,7 @@ int tts_set_step(tts_system *s, int64_t step)
     if (!s || step < 0) return fail(TTS_ERR_ARG, "bad argument");
     TTS_CUDA(cudaStreamSynchronize(s->stream), "set step");
     TTS_CUDA(cudaMemcpy(s->b.step, &step, sizeof(int64_t), cudaMemcpyHostToDevice), "write step");
+    TTS_CUDA(cudaMemset(s->b.open, 0, sizeof(int)), "reset sweep state");
     return TTS_OK;
 }
 
@@ -1325,6 +1366,7 @@ int tts_set_state(tts_system *s, const void *buf, size_t nbytes)
     TTS_CUDA(cudaStreamSynchronize(s->stream), "set state");
     o += sizeof h;
     TTS_CUDA(cudaMemcpy(s->b.step, &h[7], sizeof(int64_t), cudaMemcpyHostToDevice), "write step");
+    TTS_CUDA(cudaMemset(s->b.open, 0, sizeof(int)), "reset sweep state");
     for (void *arr : {s->b.sx, s->b.sy, s->b.sz}) {
         TTS_CUDA(cudaMemcpy(arr, o, size_t(s->n_total) * s->rsize, cudaMemcpyHostToDevice), "write spins");
         o += size_t(s->n_total) * s->rsize;

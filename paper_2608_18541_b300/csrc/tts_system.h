@@ -96,5 +96,7 @@ struct tts_system {
     int pass_block = 256;                           // general engine: threads per pass CTA
     std::vector<int> pass_blocks = {128, 256, 512}; // general engine: autotuner candidates
     void *io_buf = nullptr;                         // bulk spin I/O staging, 3 n_total reals
+    bool merged = false;                            // merged (leapfrog) sweep in use
+    bool merged_uniform = true;                     // every instance has the same colour count
 };
 
