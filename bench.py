@@ -120,12 +120,14 @@ def _traffic(kernel, precision):
     if not e:
         return None
     import hashlib
-    src = os.path.join(ROOT, "paper_2608_18541_b300", "csrc", e["source"])
+    h = hashlib.sha256()
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    except OSError:
+        for name in e["sources"]:
+            with open(os.path.join(ROOT, "paper_2608_18541_b300", "csrc", name), "rb") as f:
+                h.update(f.read())
+    except (OSError, KeyError):
         return None
-    return e["bytes_per_launch"] if h == e.get("source_sha") else None
+    return e["bytes_per_launch"] if h.hexdigest()[:16] == e.get("sources_sha") else None
 
 
 def ensemble_leg(P, W, stream, steps=200, sample=8):

@@ -346,13 +346,15 @@ __device__ __forceinline__ void pair_finish(const PairArgs &a, const PairSite &p
 // (ceil(hx / BX) * ceil(Ly/2 / BY), Lz, instances).  Registers are capped at
 // 64 (four 256-thread blocks a SM); a budget of 85 with fewer threads in
 // flight measured slower.
-template <bool AXZ>
+// SW: the launch is a leading or trailing pass of the merged sweep (compiled
+// apart so that the other passes carry none of its code).
+template <bool AXZ, bool SW>
 __global__ void __launch_bounds__(256, 4) checker_pair_kernel(PairArgs a, int colour, int hsel, int pass)
 {
     int hd = -1;
-    if (a.sw.mode != 0 && !sweep_gate(a.sw, a.step, hd)) return;
-    const bool h2 = hd == 1;          // constants made for dt/2, the bridge runs dt
-    if (hd >= 0) hsel = hd;
+    if (SW && !sweep_gate(a.sw, a.step, hd)) return;
+    const bool h2 = SW && hd == 1;    // constants made for dt/2, the bridge runs dt
+    if (SW && hd >= 0) hsel = hd;
     const uint32_t yb = blockIdx.x / a.nkx;
     const uint32_t kx = (blockIdx.x - yb * a.nkx) * blockDim.x + threadIdx.x;
     const uint32_t y2 = yb * blockDim.y + threadIdx.y;
@@ -399,14 +401,14 @@ struct TileArgs {
 
 constexpr uint64_t kBulkWaitNs = 1000000000ull;   // 1 s
 
-template <bool AXZ>
+template <bool AXZ, bool SW>
 __global__ void __launch_bounds__(256, 3) checker_pair_tiled_kernel(PairArgs a, TileArgs t, int colour, int hsel,
                                                                     int pass)
 {
     int hd = -1;
-    if (a.sw.mode != 0 && !sweep_gate(a.sw, a.step, hd)) return;
-    const bool h2 = hd == 1;
-    if (hd >= 0) hsel = hd;
+    if (SW && !sweep_gate(a.sw, a.step, hd)) return;
+    const bool h2 = SW && hd == 1;
+    if (SW && hd >= 0) hsel = hd;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_abort;
     const uint32_t hx = a.hx, by = t.by, Ly2 = a.Ly2, Lz = a.Lz;
@@ -1280,8 +1282,10 @@ bool setup_tiled(EngineState *e)
         cudaGetLastError();
         return false;
     }
-    for (const void *fn : {reinterpret_cast<const void *>(checker_pair_tiled_kernel<true>),
-                           reinterpret_cast<const void *>(checker_pair_tiled_kernel<false>)}) {
+    for (const void *fn : {reinterpret_cast<const void *>(checker_pair_tiled_kernel<true, false>),
+                           reinterpret_cast<const void *>(checker_pair_tiled_kernel<false, false>),
+                           reinterpret_cast<const void *>(checker_pair_tiled_kernel<true, true>),
+                           reinterpret_cast<const void *>(checker_pair_tiled_kernel<false, true>)}) {
         int ps = 0;
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, fn, 256, smem) != cudaSuccess || ps < 1) {
@@ -1637,17 +1641,16 @@ cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuf
         } else {
             PairArgs a = pair_args(e, p, b, hsel);
             a.sw = ctl(pass);
+            const bool sw = a.sw.mode != 0;
             if (e->bx == 0) {
-                if (e->axis_z)
-                    checker_pair_tiled_kernel<true><<<e->tile_grid, 256, e->tile_smem, st>>>(a, e->tile, c, hsel, pass);
-                else
-                    checker_pair_tiled_kernel<false><<<e->tile_grid, 256, e->tile_smem, st>>>(a, e->tile, c, hsel, pass);
+                auto fn = e->axis_z ? (sw ? checker_pair_tiled_kernel<true, true> : checker_pair_tiled_kernel<true, false>)
+                                    : (sw ? checker_pair_tiled_kernel<false, true> : checker_pair_tiled_kernel<false, false>);
+                fn<<<e->tile_grid, 256, e->tile_smem, st>>>(a, e->tile, c, hsel, pass);
             } else {
                 const dim3 pgrid(a.nkx * ((a.Ly2 + e->by - 1) / e->by), e->shape[2], e->n_inst);
-                if (e->axis_z)
-                    checker_pair_kernel<true><<<pgrid, block, 0, st>>>(a, c, hsel, pass);
-                else
-                    checker_pair_kernel<false><<<pgrid, block, 0, st>>>(a, c, hsel, pass);
+                auto fn = e->axis_z ? (sw ? checker_pair_kernel<true, true> : checker_pair_kernel<true, false>)
+                                    : (sw ? checker_pair_kernel<false, true> : checker_pair_kernel<false, false>);
+                fn<<<pgrid, block, 0, st>>>(a, c, hsel, pass);
             }
         }
         err = cudaGetLastError();
