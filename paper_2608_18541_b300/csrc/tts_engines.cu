@@ -741,7 +741,116 @@ struct ResArgs {
     int ttm_active;
     int merged;                          // merged (leapfrog) sweep
     TtmParams tp;
+    PairConsts pk;                       // FP32: constants of the pair update for h = dt/2
+    PhiloxRoundKeys rk;
+    // bath trajectory of the current chunk of steps, per instance: noise table
+    // [species][h] of each step and (T_e, T_l) after it
+    R *traj_sig;
+    double *traj_T;
+    int traj_cap;                        // steps per instance slot
+    // merged sweep across chunks of one call: colour 0 open at the end of a chunk
+    int *open_state;                     // per instance
+    int first_chunk, last_chunk;
 };
+
+// The six nearest neighbours (periodic simple-cubic) of canonical atom `at` of
+// an instance of L cells.
+__device__ __forceinline__ void resident_nbrs(uint32_t at, const ResInst &I, uint32_t nb[6])
+{
+    const int Lx = I.L[0], Ly = I.L[1], Lz = I.L[2];
+    const uint32_t z = fast_div(at, I.divxy);
+    const uint32_t rem = at - z * uint32_t(Lx * Ly);
+    const uint32_t y = fast_div(rem, I.divx);
+    const uint32_t x = rem - y * uint32_t(Lx);
+    const uint32_t xp = x + 1 == uint32_t(Lx) ? 0 : x + 1, xm = x == 0 ? Lx - 1 : x - 1;
+    const uint32_t yp = y + 1 == uint32_t(Ly) ? 0 : y + 1, ym = y == 0 ? Ly - 1 : y - 1;
+    const uint32_t zp = z + 1 == uint32_t(Lz) ? 0 : z + 1, zm = z == 0 ? Lz - 1 : z - 1;
+    nb[0] = (zp * Ly + y) * Lx + x;
+    nb[1] = (zm * Ly + y) * Lx + x;
+    nb[2] = (z * Ly + yp) * Lx + x;
+    nb[3] = (z * Ly + ym) * Lx + x;
+    nb[4] = (z * Ly + y) * Lx + xp;
+    nb[5] = (z * Ly + y) * Lx + xm;
+}
+
+// Their spin sums: all and species-1 only.
+template <typename R>
+__device__ __forceinline__ void resident_sums(uint32_t at, const ResInst &I, const R *sx, const R *sy, const R *sz,
+                                              const uint8_t *spc, R &htx, R &hty, R &htz, R &h1x, R &h1y, R &h1z)
+{
+    uint32_t nb[6];
+    resident_nbrs(at, I, nb);
+    htx = hty = htz = h1x = h1y = h1z = R(0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const R vx = sx[nb[k]], vy = sy[nb[k]], vz = sz[nb[k]];
+        const R w = spc[nb[k]] ? R(1) : R(0);
+        htx += vx;
+        hty += vy;
+        htz += vz;
+        h1x += w * vx;
+        h1y += w * vy;
+        h1z += w * vz;
+    }
+}
+
+// FP32 resident colour pass: two colour sites per thread on the packed f32x2
+// update, entry j of the colour's first half with entry j of its second half
+// (so that a warp's A lanes and B lanes each read consecutive entries); with
+// an odd count the middle entry runs in both lanes and is stored once.
+template <bool AXZ>
+__device__ __forceinline__ void resident_pair_pass(const ResArgs<float> &a, const ResInst &I, float *sx, float *sy,
+                                                   float *sz, const uint8_t *spc, int beg, int end, int64_t step,
+                                                   int p, int hsel, const float (*sig_tab)[2])
+{
+    const int half = (end - beg + 1) >> 1;
+    const bool noise = sig_tab[0][hsel] > 0.0f || sig_tab[1][hsel] > 0.0f;
+    for (int j = threadIdx.x; j < half; j += blockDim.x) {
+        const int iA = beg + j, iB0 = iA + half, iB = iB0 < end ? iB0 : iA;
+        const uint32_t atA = static_cast<uint32_t>(a.atom[I.slot_begin + iA]);
+        const uint32_t atB = static_cast<uint32_t>(a.atom[I.slot_begin + iB]);
+        f2 g1{0}, g2{0}, g3{0};
+        if (noise)
+            pair_noise(u32x4{atA, static_cast<uint32_t>(step), static_cast<uint32_t>(p), I.inst_global},
+                       u32x4{atB, static_cast<uint32_t>(step), static_cast<uint32_t>(p), I.inst_global}, a.rk, a.pk,
+                       g1, g2, g3);
+        uint32_t nA[6], nB[6];
+        resident_nbrs(atA, I, nA);
+        resident_nbrs(atB, I, nB);
+        f2 htx{0}, hty{0}, htz{0}, h1x{0}, h1y{0}, h1z{0};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const f2 vx = f2_make(sx[nA[k]], sx[nB[k]]);
+            const f2 vy = f2_make(sy[nA[k]], sy[nB[k]]);
+            const f2 vz = f2_make(sz[nA[k]], sz[nB[k]]);
+            const f2 w = f2_make(spc[nA[k]] ? 1.0f : 0.0f, spc[nB[k]] ? 1.0f : 0.0f);
+            htx = htx + vx;
+            hty = hty + vy;
+            htz = htz + vz;
+            h1x = fma2(w, vx, h1x);
+            h1y = fma2(w, vy, h1y);
+            h1z = fma2(w, vz, h1z);
+        }
+        const int tA = spc[atA], tB = spc[atB];
+        f2 px = f2_make(sx[atA], sx[atB]), py = f2_make(sy[atA], sy[atB]), pz = f2_make(sz[atA], sz[atB]);
+        const f2 w = f2_make(tA ? 1.0f : 0.0f, tB ? 1.0f : 0.0f);
+        pair_update<AXZ>(px, py, pz, htx, hty, htz, h1x, h1y, h1z, w, noise,
+                         f2_make(sig_tab[tA][hsel], sig_tab[tB][hsel]), g1, g2, g3, a.pk, hsel == 1);
+        float lx, hx_, ly, hy, lz, hz;
+        f2_split(px, lx, hx_);
+        f2_split(py, ly, hy);
+        f2_split(pz, lz, hz);
+        // same-colour sites are not neighbours: no other thread reads these until the pass ends
+        sx[atA] = lx;
+        sy[atA] = ly;
+        sz[atA] = lz;
+        if (iB != iA) {
+            sx[atB] = hx_;
+            sy[atB] = hy;
+            sz[atB] = hz;
+        }
+    }
+}
 
 // FP64 observables of the instance held in shared memory, reduced in a fixed
 // order (thread partials, warp shuffles, warps in index order).
@@ -887,7 +996,6 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<R> a, int64_t 
     uint8_t *spc = reinterpret_cast<uint8_t *>(sz + a.nmax);
     __shared__ int s_next;
     __shared__ R s_sigma[TTS_MAX_SPECIES][2];
-    __shared__ double s_T[2];
     __shared__ double warp_red[32 * 24];
     const int64_t step0 = *a.step;
     for (;;) {
@@ -905,92 +1013,60 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<R> a, int64_t 
             sz[at] = a.sz[slot];
             spc[at] = a.species[slot];
         }
-        double Te = 0.0, Tl = 0.0, deposited = 0.0;
-        const DevInstance D = a.inst[I.inst];
-        if (threadIdx.x == 0) {
-            Te = a.Te[D.cell_begin];
-            Tl = a.Tl[D.cell_begin];
-        }
+        // the bath of every step was computed before this launch
+        const R *sig_traj = a.traj_sig + int64_t(I.inst) * a.traj_cap * 4;
+        const double *T_traj = a.traj_T + int64_t(I.inst) * a.traj_cap * 2;
         __syncthreads();
-        const int Lx = I.L[0], Ly = I.L[1], Lz = I.L[2];
         // merged sweep: colour 0 left half a step ahead by the previous step
         const bool mer = a.merged && I.ncolours >= 2;
-        bool open = false;
+        bool open = mer && !a.first_chunk && a.open_state[I.inst] != 0;
         for (int64_t st = 0; st < nsteps; ++st) {
             const int64_t step = step0 + st;
-            if (threadIdx.x == 0) {
-                double T[2] = {Te, Tl};
-                resident_bath<R>(a, D, step, 0, T, &deposited, &s_sigma[0][0]);
-            }
+            if (threadIdx.x < 4) (&s_sigma[0][0])[threadIdx.x] = sig_traj[st * 4 + threadIdx.x];
             __syncthreads();
             const int K = I.ncolours;
-            const bool close =
-                !mer || st == nsteps - 1 || (a.sample_every > 0 && (step + 1) % a.sample_every == 0);
+            const bool close = !mer || (a.last_chunk && st == nsteps - 1) ||
+                               (a.sample_every > 0 && (step + 1) % a.sample_every == 0);
             for (int p = 0; p < 2 * K - 1; ++p) {
                 if (mer && p == 2 * K - 2 && !close) continue;     // the trailing half waits for the bridge
                 const int c = p < K - 1 ? p : (p == K - 1 ? K - 1 : 2 * K - 2 - p);
                 const int hsel = (p == K - 1 || (mer && p == 0 && open)) ? 1 : 0;
                 const R h = hsel ? R(a.dt) : R(0.5 * a.dt);
                 const int beg = I.colour_begin[c], end = I.colour_begin[c + 1];
-                for (int idx = beg + threadIdx.x; idx < end; idx += blockDim.x) {
-                    const uint32_t at = static_cast<uint32_t>(a.atom[I.slot_begin + idx]);
-                    const uint32_t z = fast_div(at, I.divxy);
-                    const uint32_t rem = at - z * uint32_t(Lx * Ly);
-                    const uint32_t y = fast_div(rem, I.divx);
-                    const uint32_t x = rem - y * uint32_t(Lx);
-                    const uint32_t xp = x + 1 == uint32_t(Lx) ? 0 : x + 1, xm = x == 0 ? Lx - 1 : x - 1;
-                    const uint32_t yp = y + 1 == uint32_t(Ly) ? 0 : y + 1, ym = y == 0 ? Ly - 1 : y - 1;
-                    const uint32_t zp = z + 1 == uint32_t(Lz) ? 0 : z + 1, zm = z == 0 ? Lz - 1 : z - 1;
-                    const uint32_t nb[6] = {(zp * Ly + y) * Lx + x, (zm * Ly + y) * Lx + x, (z * Ly + yp) * Lx + x,
-                                            (z * Ly + ym) * Lx + x, (z * Ly + y) * Lx + xp, (z * Ly + y) * Lx + xm};
-                    R htx = 0, hty = 0, htz = 0, h1x = 0, h1y = 0, h1z = 0;
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) {
-                        const R vx = sx[nb[k]], vy = sy[nb[k]], vz = sz[nb[k]];
-                        const R w = spc[nb[k]] ? R(1) : R(0);
-                        htx += vx;
-                        hty += vy;
-                        htz += vz;
-                        h1x += w * vx;
-                        h1y += w * vy;
-                        h1z += w * vz;
+                if constexpr (sizeof(R) == 4) {
+                    resident_pair_pass<AXZ>(a, I, sx, sy, sz, spc, beg, end, step, p, hsel, s_sigma);
+                } else {
+                    for (int idx = beg + threadIdx.x; idx < end; idx += blockDim.x) {
+                        const uint32_t at = static_cast<uint32_t>(a.atom[I.slot_begin + idx]);
+                        R htx, hty, htz, h1x, h1y, h1z;
+                        resident_sums<R>(at, I, sx, sy, sz, spc, htx, hty, htz, h1x, h1y, h1z);
+                        const int t = spc[at];
+                        const FastSpecies<R> sp = t ? a.sp[1] : a.sp[0];
+                        R s0 = sx[at], s1 = sy[at], s2 = sz[at];
+                        const R sig = s_sigma[t][hsel];
+                        if (sig > R(0)) {
+                            const u32x4 w = philox4x32_10(
+                                u32x4{at, static_cast<uint32_t>(step), static_cast<uint32_t>(p), I.inst_global}, a.key0,
+                                a.key1);
+                            fast_update<R, AXZ>(s0, s1, s2, htx, hty, htz, h1x, h1y, h1z, sp, R(a.axis[0]),
+                                                R(a.axis[1]), R(a.axis[2]), R(a.B[0]), R(a.B[1]), R(a.B[2]), sig, &w, h);
+                        } else {
+                            fast_update<R, AXZ>(s0, s1, s2, htx, hty, htz, h1x, h1y, h1z, sp, R(a.axis[0]),
+                                                R(a.axis[1]), R(a.axis[2]), R(a.B[0]), R(a.B[1]), R(a.B[2]), sig,
+                                                nullptr, h);
+                        }
+                        sx[at] = s0;
+                        sy[at] = s1;
+                        sz[at] = s2;
                     }
-                    const int t = spc[at];
-                    const FastSpecies<R> sp = t ? a.sp[1] : a.sp[0];
-                    R s0 = sx[at], s1 = sy[at], s2 = sz[at];
-                    const R sig = s_sigma[t][hsel];
-                    if (sig > R(0)) {
-                        const u32x4 w = philox4x32_10(
-                            u32x4{at, static_cast<uint32_t>(step), static_cast<uint32_t>(p), I.inst_global}, a.key0, a.key1);
-                        fast_update<R, AXZ>(s0, s1, s2, htx, hty, htz, h1x, h1y, h1z, sp, R(a.axis[0]), R(a.axis[1]),
-                                            R(a.axis[2]), R(a.B[0]), R(a.B[1]), R(a.B[2]), sig, &w, h);
-                    } else {
-                        fast_update<R, AXZ>(s0, s1, s2, htx, hty, htz, h1x, h1y, h1z, sp, R(a.axis[0]), R(a.axis[1]),
-                                            R(a.axis[2]), R(a.B[0]), R(a.B[1]), R(a.B[2]), sig, nullptr, h);
-                    }
-                    sx[at] = s0;
-                    sy[at] = s1;
-                    sz[at] = s2;
                 }
                 __syncthreads();
             }
             open = mer && !close;
-            // one-cell TTM, t_n -> t_n+1 (no diffusion on a single cell)
-            if (threadIdx.x == 0 && a.ttm_active) {
-                double T[2] = {Te, Tl};
-                resident_bath<R>(a, D, step, 1, T, &deposited, nullptr);
-                Te = T[0];
-                Tl = T[1];
-            }
-            if (a.sample_every > 0 && (step + 1) % a.sample_every == 0) {
-                if (threadIdx.x == 0) {
-                    s_T[0] = Te;
-                    s_T[1] = Tl;
-                }
-                __syncthreads();
-                resident_observe<R>(a, I, sx, sy, sz, spc, step + 1, s_T[0], s_T[1], warp_red);
-            }
+            if (a.sample_every > 0 && (step + 1) % a.sample_every == 0)
+                resident_observe<R>(a, I, sx, sy, sz, spc, step + 1, T_traj[2 * st], T_traj[2 * st + 1], warp_red);
         }
+        if (threadIdx.x == 0) a.open_state[I.inst] = open ? 1 : 0;
         for (int s = threadIdx.x; s < I.n; s += blockDim.x) {
             const int64_t slot = I.slot_begin + s;
             const int at = a.atom[slot];
@@ -1000,13 +1076,35 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<R> a, int64_t 
             a.sy[slot] = v1;
             a.sz[slot] = v2;
         }
-        if (threadIdx.x == 0) {
-            a.Te[D.cell_begin] = Te;
-            a.Tl[D.cell_begin] = Tl;
-            if (a.ttm_active) a.src_energy[I.inst] += deposited;
-        }
         __syncthreads();
     }
+}
+
+// One thread per instance: the one-cell bath of `nsteps` steps from the
+// current step -- the noise table of each step from T_e(t_n), then the
+// two-temperature advance t_n -> t_n+1 -- independent of the spins (the spins
+// do not heat the electrons), so every instance's trajectory is computed
+// before the spin kernel runs instead of serially inside it.
+template <typename R>
+__global__ void resident_traj_kernel(ResArgs<R> a, int nsteps)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_inst) return;
+    const DevInstance D = a.inst[i];
+    const int64_t step0 = *a.step;
+    double T[2] = {a.Te[D.cell_begin], a.Tl[D.cell_begin]};
+    double deposited = 0.0;
+    R *sig = a.traj_sig + int64_t(i) * a.traj_cap * 4;
+    double *TT = a.traj_T + int64_t(i) * a.traj_cap * 2;
+    for (int st = 0; st < nsteps; ++st) {
+        resident_bath<R>(a, D, step0 + st, 0, T, &deposited, sig + 4 * st);
+        if (a.ttm_active) resident_bath<R>(a, D, step0 + st, 1, T, &deposited, nullptr);
+        TT[2 * st] = T[0];
+        TT[2 * st + 1] = T[1];
+    }
+    a.Te[D.cell_begin] = T[0];
+    a.Tl[D.cell_begin] = T[1];
+    if (a.ttm_active) a.src_energy[i] += deposited;
 }
 
 __global__ void advance_step_kernel(int64_t *step, int64_t n, int *queue)
@@ -1046,6 +1144,10 @@ struct EngineState {
     ResInst *ri = nullptr;
     int *order = nullptr;
     int *queue = nullptr;
+    void *traj_sig = nullptr;        // resident: bath trajectory of a chunk of steps
+    double *traj_T = nullptr;
+    int *open_state = nullptr;
+    int traj_cap = 256;
     int nmax = 0;
     int sm_count = 0;
     int block = 256;
@@ -1450,7 +1552,12 @@ int engine_create(const tts_system_desc &d, const std::vector<HostInstance> &hos
         e->sm_count = nsm;
         if ((ce = cudaMalloc(reinterpret_cast<void **>(&e->ri), ri.size() * sizeof(ResInst))) != cudaSuccess ||
             (ce = cudaMalloc(reinterpret_cast<void **>(&e->order), order.size() * sizeof(int))) != cudaSuccess ||
-            (ce = cudaMalloc(reinterpret_cast<void **>(&e->queue), sizeof(int))) != cudaSuccess) {
+            (ce = cudaMalloc(reinterpret_cast<void **>(&e->queue), sizeof(int))) != cudaSuccess ||
+            (ce = cudaMalloc(&e->traj_sig, size_t(e->n_inst) * e->traj_cap * 4 * (d.precision == 64 ? 8 : 4))) !=
+                cudaSuccess ||
+            (ce = cudaMalloc(reinterpret_cast<void **>(&e->traj_T), size_t(e->n_inst) * e->traj_cap * 2 * sizeof(double))) !=
+                cudaSuccess ||
+            (ce = cudaMalloc(reinterpret_cast<void **>(&e->open_state), size_t(e->n_inst) * sizeof(int))) != cudaSuccess) {
             cudaGetLastError();
             engine_destroy(e);
             return eng_fail(TTS_ERR_OOM, std::string("resident buffers: ") + cudaGetErrorString(ce));
@@ -1474,7 +1581,8 @@ void engine_destroy(EngineState *e)
 {
     if (!e) return;
     for (void *q : {e->S, static_cast<void *>(e->ci), static_cast<void *>(e->ri), static_cast<void *>(e->order),
-                    static_cast<void *>(e->queue)})
+                    static_cast<void *>(e->queue), e->traj_sig, static_cast<void *>(e->traj_T),
+                    static_cast<void *>(e->open_state)})
         if (q) cudaFree(q);
     delete e;
 }
@@ -1718,7 +1826,16 @@ cudaError_t engine_run_steps(EngineState *e, const StepParams &p, const DevBuffe
         a.merged = p.merged;
         a.tp = tp;
     };
-    if (err == cudaSuccess) {
+    // chunks of at most traj_cap steps: the bath trajectory of every instance,
+    // then the spin kernel over the chunk, then the step counter
+    for (int64_t done = 0; done < nsteps && err == cudaSuccess;) {
+        const int chunk = static_cast<int>(std::min<int64_t>(nsteps - done, e->traj_cap));
+        const int tb = 128, tg = (e->n_inst + tb - 1) / tb;
+        auto chunk_args = [&](auto &a) {
+            a.open_state = e->open_state;
+            a.first_chunk = done == 0 ? 1 : 0;
+            a.last_chunk = done + chunk == nsteps ? 1 : 0;
+        };
         if (e->precision == 64) {
             ResArgs<double> a{};
             a.sx = static_cast<double *>(b.sx);
@@ -1726,10 +1843,15 @@ cudaError_t engine_run_steps(EngineState *e, const StepParams &p, const DevBuffe
             a.sz = static_cast<double *>(b.sz);
             fill(a);
             for (int t = 0; t < TTS_MAX_SPECIES; ++t) a.sp[t] = e->spd[t];
+            a.traj_sig = static_cast<double *>(e->traj_sig);
+            a.traj_T = e->traj_T;
+            a.traj_cap = e->traj_cap;
+            chunk_args(a);
+            resident_traj_kernel<double><<<tg, tb, 0, st>>>(a, chunk);
             if (e->axis_z)
-                resident_kernel<double, true><<<e->grid, e->block, e->smem, st>>>(a, nsteps);
+                resident_kernel<double, true><<<e->grid, e->block, e->smem, st>>>(a, chunk);
             else
-                resident_kernel<double, false><<<e->grid, e->block, e->smem, st>>>(a, nsteps);
+                resident_kernel<double, false><<<e->grid, e->block, e->smem, st>>>(a, chunk);
         } else {
             ResArgs<float> a{};
             a.sx = static_cast<float *>(b.sx);
@@ -1737,20 +1859,27 @@ cudaError_t engine_run_steps(EngineState *e, const StepParams &p, const DevBuffe
             a.sz = static_cast<float *>(b.sz);
             fill(a);
             for (int t = 0; t < TTS_MAX_SPECIES; ++t) a.sp[t] = e->spf[t];
+            a.pk = make_pair_consts(e, p, 0);
+            a.rk = philox_round_keys(p.key0, p.key1);
+            a.traj_sig = static_cast<float *>(e->traj_sig);
+            a.traj_T = e->traj_T;
+            a.traj_cap = e->traj_cap;
+            chunk_args(a);
+            resident_traj_kernel<float><<<tg, tb, 0, st>>>(a, chunk);
             if (e->axis_z)
-                resident_kernel<float, true><<<e->grid, e->block, e->smem, st>>>(a, nsteps);
+                resident_kernel<float, true><<<e->grid, e->block, e->smem, st>>>(a, chunk);
             else
-                resident_kernel<float, false><<<e->grid, e->block, e->smem, st>>>(a, nsteps);
+                resident_kernel<float, false><<<e->grid, e->block, e->smem, st>>>(a, chunk);
         }
         err = cudaGetLastError();
-        ++*kernels;
+        if (err == cudaSuccess) {
+            advance_step_kernel<<<1, 1, 0, st>>>(b.step, chunk, e->queue);
+            err = cudaGetLastError();
+        }
+        *kernels += 3;
+        done += chunk;
     }
     if (err == cudaSuccess && ev1) err = cudaEventRecord(ev1, st);
-    if (err == cudaSuccess) {
-        advance_step_kernel<<<1, 1, 0, st>>>(b.step, nsteps, e->queue);
-        err = cudaGetLastError();
-        ++*kernels;
-    }
     return err;
 }
 

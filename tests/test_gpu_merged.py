@@ -93,3 +93,24 @@ def test_merged_general_needs_one_colour_count():
     g = P.System(sysd, precision=64, engine="general")
     with pytest.raises(P.TTSError):
         g.step(3)
+
+
+@pytest.mark.parametrize("sweep", ["symmetric", "merged"])
+def test_resident_call_longer_than_a_bath_chunk(sweep):
+    """The resident engine advances a call in chunks of at most 256 steps (the
+    bath trajectory of every instance first, then the spins): a 300-step call
+    with sampling matches the oracle, the merged sweep staying open across
+    the chunk boundary."""
+    sysd, ttm = W.config_ensemble(n_peak=1, n_dur=1, n_real=3, lmin=5, lmax=8)
+    sysd = dict(sysd, sweep=sweep, sample_every=40)
+    g = P.System(sysd, ttm, precision=64, engine="resident")
+    assert g.engine == "resident"
+    g.step(300)
+    for i in range(3):
+        o = O.Oracle(sysd, ttm, instance=i, index=i)
+        o.step(300)
+        assert np.abs(g.get_spins(i) - o.spins()).max() <= TOL[64]
+        gs, osm = g.observables(i), o.samples()
+        assert np.array_equal(gs[:, 19], osm[:, 19])
+        assert np.allclose(gs[:, 15], osm[:, 15], rtol=1e-10)
+        assert np.allclose(gs[:, 1:7], osm[:, 1:7], atol=1e-9)
