@@ -127,6 +127,8 @@ typedef struct {
     int instance_base;           /* global id of instance 0 (Philox counter word 3 and
                                     placement stream are keyed by instance_base + index) */
     int sweep;                   /* TTS_SWEEP_* */
+    const double *inst_T_bath;   /* NULL or n_instances bath temperatures used while no TTM
+                                    grid is set, K (e.g. a temperature scan in one batch) */
 } tts_system_desc;
 
 #define TTS_SOURCE_NONE 0

@@ -217,7 +217,7 @@ def _fill_params(sysd, instance, index, noise_mu_power):
         p.axis[k] = float(sysd["axis"][k])
         p.B[k] = float(sysd["B"][k])
     p.dt = float(sysd["dt"])
-    p.T_bath = float(sysd.get("T_bath", 0.0))
+    p.T_bath = float(over.get("T_bath", sysd.get("T_bath", 0.0)))
     p.seed = int(sysd["seed"])
     p.instance = int(instance)
     p.sample_every = int(sysd.get("sample_every", 0))

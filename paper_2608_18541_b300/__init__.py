@@ -54,7 +54,7 @@ class tts_system_desc(C.Structure):
         ("obs_capacity", C.c_int), ("n_instances", C.c_int), ("inst_cells", C.POINTER(C.c_int)),
         ("inst_frac1", C.POINTER(C.c_double)), ("inst_peak_Te", C.POINTER(C.c_double)),
         ("inst_fwhm", C.POINTER(C.c_double)), ("engine", C.c_int), ("instance_base", C.c_int),
-        ("sweep", C.c_int),
+        ("sweep", C.c_int), ("inst_T_bath", C.POINTER(C.c_double)),
     ]
 
 
@@ -213,6 +213,10 @@ def make_desc(sysd, precision=64, engine="auto", obs_capacity=0, instance_base=0
             fw = np.array([i["fwhm"] for i in inst], dtype=np.float64)
             keep.append(fw)
             d.inst_fwhm = _dp(fw)
+        if any("T_bath" in i for i in inst):
+            tb = np.array([float(i.get("T_bath", sysd.get("T_bath", 0.0))) for i in inst], dtype=np.float64)
+            keep.append(tb)
+            d.inst_T_bath = _dp(tb)
     else:
         d.n_instances = 1
     return d, keep

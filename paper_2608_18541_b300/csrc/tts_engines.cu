@@ -189,6 +189,7 @@ struct PairArgs {
     int64_t n_inst_sites;
     uint32_t inst_base;
     int noise;                   // some species has alpha > 0 (else sigma = 0 everywhere)
+    int n_inst;
     // TTM cell of a site from its coordinates, cell0 + inst cstride +
     // (cz ncy + cy) ncx + cx with c_k = floor(k n_k / L_k); the host checks it
     // against the cell map, else cell_formula = 0 and the map is read.
@@ -346,22 +347,17 @@ __device__ __forceinline__ void pair_finish(const PairArgs &a, const PairSite &p
 // (ceil(hx / BX) * ceil(Ly/2 / BY), Lz, instances).  Registers are capped at
 // 64 (four 256-thread blocks a SM); a budget of 85 with fewer threads in
 // flight measured slower.
-// SW: the launch is a leading or trailing pass of the merged sweep (compiled
-// apart so that the other passes carry none of its code).
-template <bool AXZ, bool SW>
-__global__ void __launch_bounds__(256, 4) checker_pair_kernel(PairArgs a, int colour, int hsel, int pass)
+// One block's worth of pairs: block index bx of a row of blocks (BX pairs x
+// BY pair rows), plane z, instance inst.
+template <bool AXZ>
+__device__ __forceinline__ void pair_block(const PairArgs &a, int colour, int hsel, bool h2, int pass, uint32_t bx,
+                                           uint32_t z, int inst)
 {
-    int hd = -1;
-    if (SW && !sweep_gate(a.sw, a.step, hd)) return;
-    const bool h2 = SW && hd == 1;    // constants made for dt/2, the bridge runs dt
-    if (SW && hd >= 0) hsel = hd;
-    const uint32_t yb = blockIdx.x / a.nkx;
-    const uint32_t kx = (blockIdx.x - yb * a.nkx) * blockDim.x + threadIdx.x;
+    const uint32_t yb = bx / a.nkx;
+    const uint32_t kx = (bx - yb * a.nkx) * blockDim.x + threadIdx.x;
     const uint32_t y2 = yb * blockDim.y + threadIdx.y;
     const uint32_t hx = a.hx, Ly2 = a.Ly2, Lz = a.Lz;
     if (y2 >= Ly2 || kx >= hx) return;
-    const uint32_t z = blockIdx.y;
-    const int inst = blockIdx.z;
     const PairSite p = make_site(a, inst, z, y2, kx, colour);
     f2 g1{0}, g2{0}, g3{0};
     if (a.noise) site_noise(a, p, static_cast<uint32_t>(*a.step), pass, g1, g2, g3);
@@ -378,6 +374,30 @@ __global__ void __launch_bounds__(256, 4) checker_pair_kernel(PairArgs a, int co
                    (z * Ly2 + yp) * hx, (z * Ly2 + ym) * hx, htx, hty, htz, h1x, h1y, h1z);
     const uint32_t q = r0 + kx;
     pair_finish<AXZ>(a, p, colour, hsel, h2, g1, g2, g3, htx, hty, htz, h1x, h1y, h1z, Wlo[q], Whi[q], Wlo, Whi, q);
+}
+
+// SW: the launch is a leading or trailing pass of the merged sweep (compiled
+// apart so that the other passes carry none of its code).  Those run on a
+// persistent grid that walks the (row block, z, instance) blocks, so that a
+// trailing pass the sweep skips costs one early exit per resident CTA.
+template <bool AXZ, bool SW>
+__global__ void __launch_bounds__(256, 4) checker_pair_kernel(PairArgs a, int colour, int hsel, int pass)
+{
+    if (!SW) {
+        pair_block<AXZ>(a, colour, hsel, false, pass, blockIdx.x, blockIdx.y, blockIdx.z);
+        return;
+    }
+    int hd = -1;
+    if (!sweep_gate(a.sw, a.step, hd)) return;
+    const bool h2 = hd == 1;          // constants made for dt/2, the bridge runs dt
+    if (hd >= 0) hsel = hd;
+    const uint32_t nbx = a.nkx * ((a.Ly2 + blockDim.y - 1) / blockDim.y);
+    const uint64_t nvb = uint64_t(nbx) * a.Lz * uint64_t(a.n_inst);
+    for (uint64_t v = blockIdx.x; v < nvb; v += gridDim.x) {
+        const uint32_t bx = static_cast<uint32_t>(v % nbx);
+        const uint64_t r = v / nbx;
+        pair_block<AXZ>(a, colour, hsel, h2, pass, bx, static_cast<uint32_t>(r % a.Lz), static_cast<int>(r / a.Lz));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1455,6 +1475,14 @@ int engine_create(const tts_system_desc &d, const std::vector<HostInstance> &hos
         for (int k = 0; k < 3; ++k) e->shape[k] = static_cast<uint32_t>(host[0].cells[k]);
         e->inst_base = static_cast<uint32_t>(d.instance_base);
         e->pair = d.precision == 32;
+        {
+            int dev = 0, nsm = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+                e->sm_count = nsm;
+            else
+                cudaGetLastError();
+        }
         // x rows of hx = Lx/2 colour sites in warps, the rest of the threads in y
         const int hxs = static_cast<int>(e->shape[0] / 2);
         if (e->pair) {
@@ -1635,6 +1663,7 @@ PairArgs pair_args(const EngineState *e, const StepParams &p, const DevBuffers &
     a.n_inst_sites = e->n_total / e->n_inst;
     a.inst_base = e->inst_base;
     a.noise = e->noise ? 1 : 0;
+    a.n_inst = e->n_inst;
     a.cell_formula = e->cell_formula;
     a.cell0 = e->cell0;
     a.cstride = e->cstride;
@@ -1758,7 +1787,15 @@ cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuf
                 const dim3 pgrid(a.nkx * ((a.Ly2 + e->by - 1) / e->by), e->shape[2], e->n_inst);
                 auto fn = e->axis_z ? (sw ? checker_pair_kernel<true, true> : checker_pair_kernel<true, false>)
                                     : (sw ? checker_pair_kernel<false, true> : checker_pair_kernel<false, false>);
-                fn<<<pgrid, block, 0, st>>>(a, c, hsel, pass);
+                if (sw) {
+                    // one block per (row block, z, instance) for the leading pass; the
+                    // trailing pass, often skipped, on a persistent grid of 8 CTAs a SM
+                    const uint64_t nvb = uint64_t(pgrid.x) * pgrid.y * pgrid.z;
+                    const uint64_t cap = a.sw.mode == 2 ? uint64_t(e->sm_count > 0 ? e->sm_count : 148) * 8 : nvb;
+                    fn<<<static_cast<unsigned>(std::min(nvb, cap)), block, 0, st>>>(a, c, hsel, pass);
+                } else {
+                    fn<<<pgrid, block, 0, st>>>(a, c, hsel, pass);
+                }
             }
         }
         err = cudaGetLastError();

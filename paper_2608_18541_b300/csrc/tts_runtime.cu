@@ -87,6 +87,9 @@ int validate(const tts_system_desc &d)
             if (x.kind == TTS_EXCH_BETHE_SLATER && !(x.J3 > 0.0)) return fail(TTS_ERR_ARG, "J3 must be positive");
         }
     if (!(d.T_bath >= 0.0)) return fail(TTS_ERR_ARG, "T_bath must be >= 0");
+    if (d.inst_T_bath)
+        for (int i = 0; i < d.n_instances; ++i)
+            if (!(d.inst_T_bath[i] >= 0.0)) return fail(TTS_ERR_ARG, "instance bath temperatures must be >= 0");
     if (d.engine < 0 || d.engine > 3) return fail(TTS_ERR_ARG, "unknown engine");
     if (d.sample_every < 0) return fail(TTS_ERR_ARG, "sample_every must be >= 0");
     if (d.instance_base < 0) return fail(TTS_ERR_ARG, "instance_base must be >= 0");
@@ -477,6 +480,7 @@ int tts_create_system(const tts_system_desc *desc, void *stream, tts_system **ou
     s->desc.inst_frac1 = nullptr;
     s->desc.inst_peak_Te = nullptr;
     s->desc.inst_fwhm = nullptr;
+    s->desc.inst_T_bath = nullptr;
     if (desc->inst_peak_Te) s->inst_peak.assign(desc->inst_peak_Te, desc->inst_peak_Te + s->n_inst);
     if (desc->inst_fwhm) s->inst_fwhm.assign(desc->inst_fwhm, desc->inst_fwhm + s->n_inst);
 
@@ -641,6 +645,8 @@ int tts_create_system(const tts_system_desc *desc, void *stream, tts_system **ou
         if ((rc = upload(b.obs_block_begin, bb.data(), bb.size() * sizeof(int64_t), s->stream, "upload obs blocks"))) return rc;
     }
     std::vector<double> Tb(s->n_inst, desc->T_bath), ones(s->n_inst, 1.0);
+    if (desc->inst_T_bath)
+        for (int i = 0; i < s->n_inst; ++i) Tb[i] = desc->inst_T_bath[i];
     if ((rc = upload(b.Te, Tb.data(), Tb.size() * sizeof(double), s->stream, "upload bath"))) return rc;
     if ((rc = upload(b.Tl, Tb.data(), Tb.size() * sizeof(double), s->stream, "upload bath"))) return rc;
     if ((rc = upload(b.src_shape, ones.data(), ones.size() * sizeof(double), s->stream, "upload shape"))) return rc;

@@ -173,3 +173,13 @@ def config_moving_fe(n=40):
     lat = morse_fe_lattice()
     ttm = ttm_z_exp((10, 10, 40), 1500.0, 100 * FS, 0.25, Lz=n * 2.8665)
     return s, ttm, lat
+
+
+def curie_scan(temps, n=6, reps=2, alpha=0.5, dt=1.0 * FS, seed=42):
+    """Batched temperature scan of rigid bcc Fe (one uniform bath per
+    instance): len(temps) x reps instances of n^3 cells, instance k at
+    temps[k // reps]."""
+    s = bcc_fe(n, T=float(temps[0]), steps_dt=dt, seed=seed, alpha=alpha)
+    s["instances"] = [{"nx": n, "ny": n, "nz": n, "frac1": 0.0, "T_bath": float(T)}
+                      for T in temps for _ in range(reps)]
+    return s
