@@ -134,6 +134,12 @@ typedef struct {
 #define TTS_SOURCE_NONE 0
 #define TTS_SOURCE_PEAK 1          /* calibrate P0 so that max T_e over cells and steps = peak_Te */
 #define TTS_SOURCE_POWER 2         /* use P0 as given */
+#define TTS_SOURCE_STEP_PROFILE 3  /* prescribed electron temperature, the three-stage step profile
+                                      of the paper's GdFeCo runs (Sec. II.E): T_e = peak_Te for
+                                      t < t0, peak_Te / 2 for t0 <= t < t0 + fwhm, T0 after; T_l = T0.
+                                      No grid equation (gamma_e, C_l, G, kappa_e unused); peak_Te
+                                      and fwhm (the second stage) take the per-instance overrides;
+                                      not with a moving lattice. */
 
 #define TTS_SPATIAL_UNIFORM 0
 #define TTS_SPATIAL_XY_GAUSS 1     /* exp(-((x-xc)^2 + (y-yc)^2) / (2 sigma_xy^2)) at cell centres */

@@ -56,7 +56,7 @@ class _Lattice(C.Structure):
 
 _LATTICE = {"sc": 0, "bcc": 1, "fcc": 2, "cluster": 3}
 _EXKIND = {"none": 0, "const": 1, "bethe_slater": 2}
-_SOURCE = {"none": 0, "peak": 1, "power": 2}
+_SOURCE = {"none": 0, "peak": 1, "power": 2, "step_profile": 3}
 _SPATIAL = {"uniform": 0, "xy_gauss": 1, "z_exp": 2}
 
 

@@ -533,9 +533,22 @@ static int cidx(const orc_sys *S, int cx, int cy, int cz)
  * on the given grids; returns the source energy deposited (J). */
 /* use_G = 0 drops the G (T_e - T_l) exchange: with a moving lattice the ions
  * exchange energy with the electrons through their own friction and noise. */
+/* The three-stage electron-temperature profile of the paper's GdFeCo runs
+ * (Sec. II.E): peak, half the peak, then the base temperature. */
+static double profile_Te(const orc_ttm *t, double tt)
+{
+    if (tt < t->t0) return t->peak_Te;
+    if (tt < t->t0 + t->fwhm) return 0.5 * t->peak_Te;
+    return t->T0;
+}
+
 static double ttm_advance(const orc_sys *S, double *Te, double *Tl, double t_start, double Dt, double P0, int use_G)
 {
     const orc_ttm *t = &S->t;
+    if (t->source == 3) {
+        for (int c = 0; c < S->nc; ++c) { Te[c] = profile_Te(t, t_start + Dt); Tl[c] = t->T0; }
+        return 0.0;
+    }
     int m = S->substeps;
     double dl = Dt / m;
     double sig = pulse_sigma(t), t0 = pulse_t0(t);
@@ -616,7 +629,10 @@ int orc_set_ttm(orc_sys *S, const orc_ttm *t, char *err, int errlen)
     int nl[3] = {S->p.nx, S->p.ny, S->p.nz};
     for (int d = 0; d < 3; ++d) S->dxc[d] = S->box[d] * ANG / nd[d];
     S->cellvol = S->dxc[0] * S->dxc[1] * S->dxc[2];
-    for (int c = 0; c < S->nc; ++c) { S->Te[c] = t->T0; S->Tl[c] = t->T0; }
+    for (int c = 0; c < S->nc; ++c) {
+        S->Te[c] = t->source == 3 ? profile_Te(t, S->step * ttm_dt(S)) : t->T0;
+        S->Tl[c] = t->T0;
+    }
     /* cell of atom: floor(x / L * n) evaluated exactly on the half-lattice
      * integer coordinate, so atoms on a cell face go to the upper cell */
     for (int i = 0; i < S->n; ++i) {
@@ -642,7 +658,7 @@ int orc_set_ttm(orc_sys *S, const orc_ttm *t, char *err, int errlen)
     double dxmin = 1e300;
     for (int k = 0; k < 3; ++k) if (nd[k] > 1) { ++d; if (S->dxc[k] < dxmin) dxmin = S->dxc[k]; }
     S->substeps = 1;
-    if (d > 0 && t->kappa_e > 0.0) {
+    if (d > 0 && t->kappa_e > 0.0 && t->source != 3) {
         double dmax = 0.4 * t->gamma_e * t->T0 * dxmin * dxmin / (t->kappa_e * d);
         double m = ceil(ttm_dt(S) / dmax);
         S->substeps = m < 1.0 ? 1 : (int)m;

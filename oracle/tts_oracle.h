@@ -56,7 +56,9 @@ typedef struct {
     double G;               /* electron-phonon coupling, W m^-3 K^-1 */
     double kappa_e;         /* electron conductivity, W m^-1 K^-1 */
     double T0;              /* initial T_e = T_l, K */
-    int source;             /* 0 none, 1 calibrate P0 to peak_Te, 2 fixed P0 */
+    int source;             /* 0 none, 1 calibrate P0 to peak_Te, 2 fixed P0, 3 step profile:
+                               T_e = peak_Te for t < t0, peak_Te / 2 for t0 <= t < t0 + fwhm,
+                               T0 after; T_l = T0 (prescribed, no grid equation) */
     double peak_Te;         /* K */
     double P0;              /* W m^-3 */
     double fwhm;            /* s */

@@ -26,7 +26,7 @@ LATTICE = {"sc": 0, "bcc": 1, "fcc": 2, "cluster": 3}
 EXCH = {"none": 0, "const": 1, "bethe_slater": 2}
 ENGINE = {"auto": 0, "general": 1, "checker": 2, "resident": 3}
 ENGINE_NAME = {v: k for k, v in ENGINE.items()}
-SOURCE = {"none": 0, "peak": 1, "power": 2}
+SOURCE = {"none": 0, "peak": 1, "power": 2, "step_profile": 3}
 SPATIAL = {"uniform": 0, "xy_gauss": 1, "z_exp": 2}
 
 

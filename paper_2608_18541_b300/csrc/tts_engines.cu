@@ -987,6 +987,12 @@ __device__ __noinline__ void resident_bath(const ResArgs<R> &a, const DevInstanc
             }
         return;
     }
+    if (a.tp.source == TTS_SOURCE_STEP_PROFILE) {
+        const double tt = double(step + 1) * a.dt;
+        T[0] = tt < D.prof_t1 ? D.prof_peak : (tt < D.prof_t2 ? 0.5 * D.prof_peak : a.tp.T0);
+        T[1] = a.tp.T0;
+        return;
+    }
     double Te = T[0], Tl = T[1];
     const double delta = a.dt / D.substeps;
     for (int k = 0; k < D.substeps; ++k) {

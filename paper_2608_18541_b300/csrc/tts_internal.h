@@ -59,6 +59,7 @@ struct DevInstance {
     int substeps;                       // TTM sub-steps per spin step
     double P0;                          // W m^-3
     double sigma_t, t0;                 // s
+    double prof_peak, prof_t1, prof_t2; // step profile: peak T_e (K), end of stage 1, end of stage 2 (s)
     double dx[3];                       // m
     double cell_volume;                 // m^3
     int obs_block_begin;                // first observable partial block

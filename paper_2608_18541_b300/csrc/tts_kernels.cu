@@ -324,6 +324,27 @@ __global__ void ttm_apply_kernel(StepParams p, DevBuffers b, TtmParams tp, int n
     write_sigma<R>(p, T, static_cast<R *>(b.sigma), g);
 }
 
+// Prescribed three-stage T_e (step profile) at time t.
+__device__ __forceinline__ double profile_Te(const DevInstance &I, double t, double T_base)
+{
+    return t < I.prof_t1 ? I.prof_peak : (t < I.prof_t2 ? 0.5 * I.prof_peak : T_base);
+}
+
+// Step profile: T_e of every cell at t_n+1 and the noise table of the next
+// step from it; T_l stays at the base temperature.
+template <typename R>
+__global__ void ttm_profile_kernel(StepParams p, DevBuffers b, TtmParams tp, const int *__restrict__ cell_inst,
+                                   int ncells_total)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ncells_total) return;
+    const DevInstance &I = b.inst[cell_inst[g]];
+    const double T = profile_Te(I, double(*b.step + 1) * p.dt, tp.T0);
+    b.Te[g] = T;
+    b.Tl[g] = tp.T0;
+    write_sigma<R>(p, T, static_cast<R *>(b.sigma), g);
+}
+
 // ---------------------------------------------------------------------------
 // Observables.  mode 0: inside a step (sample when (step+1) % every == 0, into
 // the ring, then advance the step counter); mode 1: now, into obs_now.
@@ -590,6 +611,16 @@ cudaError_t launch_set_target(const DevBuffers &b, int64_t n, cudaStream_t st)
 cudaError_t launch_ttm(const StepParams &p, const DevBuffers &b, const TtmParams &tp, int n_instances,
                        cudaStream_t st, int precision, int inc_step)
 {
+    if (b.cell_inst && tp.source == TTS_SOURCE_STEP_PROFILE) {
+        const int n = p.ncells_total;
+        if (precision == 64)
+            ttm_profile_kernel<double><<<(n + 255) / 256, 256, 0, st>>>(p, b, tp, b.cell_inst, n);
+        else
+            ttm_profile_kernel<float><<<(n + 255) / 256, 256, 0, st>>>(p, b, tp, b.cell_inst, n);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess || !inc_step) return e;
+        return launch_step_inc(b, st);
+    }
     if (b.cell_inst && p.ttm_one_substep) {
         const int n = p.ncells_total;
         ttm_increment_kernel<<<(n + 255) / 256, 256, 0, st>>>(p, b, tp, b.cell_inst, n);

@@ -678,7 +678,10 @@ int tts_set_ttm_grid(tts_system *s, const tts_ttm_desc *t)
         if (t->cells[k] < 1) return fail(TTS_ERR_ARG, "TTM cell counts must be >= 1");
     if (!(t->gamma_e > 0.0) || !(t->C_l > 0.0) || !(t->G >= 0.0) || !(t->kappa_e >= 0.0) || !(t->T0 > 0.0))
         return fail(TTS_ERR_ARG, "TTM coefficients out of range");
-    if (t->source < 0 || t->source > 2 || t->spatial < 0 || t->spatial > 2) return fail(TTS_ERR_ARG, "bad TTM mode");
+    if (t->source < 0 || t->source > 3 || t->spatial < 0 || t->spatial > 2) return fail(TTS_ERR_ARG, "bad TTM mode");
+    const bool profile = t->source == TTS_SOURCE_STEP_PROFILE;
+    if (profile && s->lat) return fail(TTS_ERR_UNSUPPORTED, "the step profile is for rigid lattices");
+    if (profile && !(t->t0 >= 0.0)) return fail(TTS_ERR_ARG, "step profile: t0 (first stage) must be >= 0");
     TTS_CUDA(cudaStreamSynchronize(s->stream), "set ttm");
     const int nc = t->cells[0] * t->cells[1] * t->cells[2];
     const int total = nc * s->n_inst;
@@ -698,9 +701,11 @@ int tts_set_ttm_grid(tts_system *s, const tts_ttm_desc *t)
         DevInstance &di = s->dinst[i];
         const double my_fwhm = s->inst_fwhm.empty() ? t->fwhm : s->inst_fwhm[i];
         const double my_peak = s->inst_peak.empty() ? t->peak_Te : s->inst_peak[i];
-        if (t->source != TTS_SOURCE_NONE && !(my_fwhm > 0.0)) return fail(TTS_ERR_ARG, "pulse FWHM must be positive");
+        if (profile && !(my_fwhm >= 0.0 && my_peak >= 0.0))
+            return fail(TTS_ERR_ARG, "step profile: peak and second-stage duration must be >= 0");
+        if (!profile && t->source != TTS_SOURCE_NONE && !(my_fwhm > 0.0)) return fail(TTS_ERR_ARG, "pulse FWHM must be positive");
         HostTtm &h = hts[i];
-        make_host_ttm(lattice_step_length(s), hi, *t, t->source != TTS_SOURCE_NONE ? my_fwhm : 1.0, &h);
+        make_host_ttm(lattice_step_length(s), hi, *t, t->source != TTS_SOURCE_NONE && !profile ? my_fwhm : 1.0, &h);
         if (t->source == TTS_SOURCE_PEAK) {
             if (!(my_peak > t->T0)) return fail(TTS_ERR_ARG, "peak T_e must exceed T0");
             // a one-cell grid has no length scale: its calibration ignores the box
@@ -721,7 +726,10 @@ int tts_set_ttm_grid(tts_system *s, const tts_ttm_desc *t)
             di.dx[k] = h.dx[k];
         }
         di.cell_volume = h.vol;
-        di.substeps = h.substeps;
+        di.substeps = profile ? 1 : h.substeps;
+        di.prof_peak = my_peak;
+        di.prof_t1 = t->t0;
+        di.prof_t2 = t->t0 + my_fwhm;
         di.P0 = t->P0;
         di.sigma_t = h.sigma_t;
         di.t0 = h.t0;
@@ -860,8 +868,20 @@ int tts_set_ttm_grid(tts_system *s, const tts_ttm_desc *t)
         if ((rc = upload(b.cell_inst, ci.data(), ci.size() * sizeof(int), s->stream, "upload cell instances"))) return rc;
         s->p.ttm_one_substep = one && !s->lat ? 1 : 0;
     }
+    std::vector<double> Tl0(Te);
+    if (profile) {
+        // the profile at the current time
+        int64_t step = 0;
+        TTS_CUDA(cudaMemcpy(&step, b.step, sizeof step, cudaMemcpyDeviceToHost), "read step");
+        const double tt = double(step) * s->desc.dt;
+        for (int i = 0; i < s->n_inst; ++i) {
+            const DevInstance &di = s->dinst[i];
+            const double T = tt < di.prof_t1 ? di.prof_peak : (tt < di.prof_t2 ? 0.5 * di.prof_peak : t->T0);
+            for (int c = 0; c < nc; ++c) Te[i * nc + c] = T;
+        }
+    }
     if ((rc = upload(b.Te, Te.data(), total * sizeof(double), s->stream, "upload T_e"))) return rc;
-    if ((rc = upload(b.Tl, Te.data(), total * sizeof(double), s->stream, "upload T_l"))) return rc;
+    if ((rc = upload(b.Tl, Tl0.data(), total * sizeof(double), s->stream, "upload T_l"))) return rc;
     if ((rc = upload(b.src_shape, shape.data(), total * sizeof(double), s->stream, "upload shape"))) return rc;
     if ((rc = upload(b.cell, cellmap.data(), cellmap.size() * sizeof(int), s->stream, "upload cell map"))) return rc;
     if ((rc = upload(b.inst, s->dinst.data(), s->dinst.size() * sizeof(DevInstance), s->stream, "upload instances"))) return rc;
