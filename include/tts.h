@@ -129,6 +129,11 @@ typedef struct {
     int sweep;                   /* TTS_SWEEP_* */
     const double *inst_T_bath;   /* NULL or n_instances bath temperatures used while no TTM
                                     grid is set, K (e.g. a temperature scan in one batch) */
+    double colour_rc;            /* 0, or a distance (angstrom) above the largest exchange
+                                    cutoff: no two atoms closer than it share a colour class
+                                    (the lattice rule when it qualifies, else greedy); the
+                                    margin a moving lattice needs so that no exchange pair
+                                    joins one colour as the atoms move */
 } tts_system_desc;
 
 #define TTS_SOURCE_NONE 0

@@ -33,7 +33,7 @@ class _Params(C.Structure):
         ("B", C.c_double * 3), ("alpha", C.c_double * 2), ("dt", C.c_double),
         ("T_bath", C.c_double), ("init_dir", (C.c_double * 3) * 2), ("seed", C.c_uint64),
         ("instance", C.c_uint32), ("sample_every", C.c_int), ("noise_mu_power", C.c_double),
-        ("sweep", C.c_int),
+        ("sweep", C.c_int), ("colour_rc", C.c_double),
     ]
 
 
@@ -223,6 +223,7 @@ def _fill_params(sysd, instance, index, noise_mu_power):
     p.sample_every = int(sysd.get("sample_every", 0))
     p.noise_mu_power = float(noise_mu_power)
     p.sweep = {"symmetric": 0, "merged": 1}[sysd.get("sweep", "symmetric")]
+    p.colour_rc = float(sysd.get("colour_rc", 0.0))
     return p, keep
 
 

@@ -356,11 +356,11 @@ static int build_neighbours(orc_sys *S, char *err, int errlen)
  * otherwise greedy colouring in ascending atom id (each atom takes the smallest
  * colour unused by its already-coloured neighbours).  No neighbours at all:
  * a single colour. */
-static int colouring_valid(const orc_sys *S, const int *col)
+static int colouring_valid(int n, const int *start, const int *adj, const int *col)
 {
-    for (int i = 0; i < S->n; ++i)
-        for (int k = S->nbr_start[i]; k < S->nbr_start[i + 1]; ++k)
-            if (col[S->nbr_j[k]] == col[i]) return 0;
+    for (int i = 0; i < n; ++i)
+        for (int k = start[i]; k < start[i + 1]; ++k)
+            if (col[adj[k]] == col[i]) return 0;
     return 1;
 }
 
@@ -370,11 +370,44 @@ static int cycle3(int x, int L)
     return x % 3;
 }
 
+/* The graph to colour: the exchange neighbours, or, with colour_rc above the
+ * exchange cutoff, every pair closer than colour_rc (minimum image; all pairs
+ * checked). */
+static void colour_graph(const orc_sys *S, int **start_out, int **adj_out)
+{
+    int n = S->n;
+    if (!(S->p.colour_rc > max_rc(&S->p))) {
+        *start_out = NULL;
+        *adj_out = NULL;
+        return;
+    }
+    int *start = malloc(sizeof(int) * (n + 1)), cap = 16 * n + 16, tot = 0;
+    int *adj = malloc(sizeof(int) * cap);
+    for (int i = 0; i < n; ++i) {
+        start[i] = tot;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3];
+            min_image(S, i, j, d);
+            if (sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) < S->p.colour_rc) {
+                if (tot == cap) { cap *= 2; adj = realloc(adj, sizeof(int) * cap); }
+                adj[tot++] = j;
+            }
+        }
+    }
+    start[n] = tot;
+    *start_out = start;
+    *adj_out = adj;
+}
+
 static void build_colours(orc_sys *S)
 {
     int n = S->n;
     S->colour = calloc(n, sizeof(int));
     if (S->nbr_start[n] == 0) { S->ncolours = 1; return; }
+    int *gs, *ga;
+    colour_graph(S, &gs, &ga);
+    const int *start = gs ? gs : S->nbr_start, *adj = gs ? ga : S->nbr_j;
     int rule = 0, K = 0;
     if (S->p.lattice <= 2) {
         int nb = basis_count(S->p.lattice);
@@ -390,24 +423,29 @@ static void build_colours(orc_sys *S)
             else S->colour[i] = b;
         }
         K = S->p.lattice == 0 ? (even ? 2 : 3) : 4;
-        rule = colouring_valid(S, S->colour);
+        rule = colouring_valid(n, start, adj, S->colour);
     }
-    if (rule) { S->ncolours = K; return; }
-    int maxc = 0;
-    int *used = calloc(n + 1, sizeof(int));
-    for (int i = 0; i < n; ++i) S->colour[i] = -1;
-    for (int i = 0; i < n; ++i) {
-        for (int k = S->nbr_start[i]; k < S->nbr_start[i + 1]; ++k) {
-            int c = S->colour[S->nbr_j[k]];
-            if (c >= 0) used[c] = i + 1;
+    if (rule) {
+        S->ncolours = K;
+    } else {
+        int maxc = 0;
+        int *used = calloc(n + 1, sizeof(int));
+        for (int i = 0; i < n; ++i) S->colour[i] = -1;
+        for (int i = 0; i < n; ++i) {
+            for (int k = start[i]; k < start[i + 1]; ++k) {
+                int c = S->colour[adj[k]];
+                if (c >= 0) used[c] = i + 1;
+            }
+            int c = 0;
+            while (used[c] == i + 1) ++c;
+            S->colour[i] = c;
+            if (c + 1 > maxc) maxc = c + 1;
         }
-        int c = 0;
-        while (used[c] == i + 1) ++c;
-        S->colour[i] = c;
-        if (c + 1 > maxc) maxc = c + 1;
+        free(used);
+        S->ncolours = maxc;
     }
-    free(used);
-    S->ncolours = maxc;
+    free(gs);
+    free(ga);
 }
 
 /* Random alloy, Sec. II.D: exactly round(frac1 * N) sites take species 1,

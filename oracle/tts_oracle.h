@@ -47,6 +47,8 @@ typedef struct {
     int sample_every;       /* record observables every this many steps (0 = never) */
     double noise_mu_power;  /* 0.5: FDT noise ~ mu^-1/2; 1: the variant without mu_fdt */
     int sweep;              /* 0 symmetric sweep per step; 1 merged sweep (see orc_step) */
+    double colour_rc;       /* 0, or a distance (angstrom) above the exchange cutoff within
+                               which no two atoms share a colour */
 } orc_params;
 
 typedef struct {

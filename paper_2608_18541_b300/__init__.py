@@ -54,7 +54,7 @@ class tts_system_desc(C.Structure):
         ("obs_capacity", C.c_int), ("n_instances", C.c_int), ("inst_cells", C.POINTER(C.c_int)),
         ("inst_frac1", C.POINTER(C.c_double)), ("inst_peak_Te", C.POINTER(C.c_double)),
         ("inst_fwhm", C.POINTER(C.c_double)), ("engine", C.c_int), ("instance_base", C.c_int),
-        ("sweep", C.c_int), ("inst_T_bath", C.POINTER(C.c_double)),
+        ("sweep", C.c_int), ("inst_T_bath", C.POINTER(C.c_double)), ("colour_rc", C.c_double),
     ]
 
 
@@ -196,6 +196,7 @@ def make_desc(sysd, precision=64, engine="auto", obs_capacity=0, instance_base=0
     d.engine = ENGINE[engine] if isinstance(engine, str) else int(engine)
     d.instance_base = int(instance_base)
     d.sweep = {"symmetric": 0, "merged": 1}[sysd.get("sweep", "symmetric")]
+    d.colour_rc = float(sysd.get("colour_rc", 0.0))
     inst = sysd.get("instances")
     if inst:
         d.n_instances = len(inst)

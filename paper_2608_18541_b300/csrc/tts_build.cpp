@@ -143,11 +143,75 @@ void neighbours_cluster(const tts_system_desc &d, HostInstance *hi)
     }
 }
 
-bool proper(const HostInstance &hi, const std::vector<int> &col)
+// Graph of the colouring: CSR adjacency, ascending neighbour ids.
+struct ColourGraph {
+    std::vector<int64_t> begin;
+    std::vector<int> adj;
+};
+
+// Every pair closer than rc (geometric, periodic lattice or open cluster).
+ColourGraph pairs_within(const tts_system_desc &d, const HostInstance &hi, double rc)
 {
-    for (int64_t i = 0; i < hi.n; ++i)
-        for (int64_t k = hi.nbr_begin[i]; k < hi.nbr_begin[i + 1]; ++k)
-            if (col[hi.nbr[k]] == col[i]) return false;
+    ColourGraph g;
+    g.begin.assign(hi.n + 1, 0);
+    std::vector<int64_t> row;
+    if (d.lattice == TTS_LATTICE_CLUSTER) {
+        for (int64_t i = 0; i < hi.n; ++i) {
+            for (int64_t j = 0; j < hi.n; ++j) {
+                if (j == i) continue;
+                double r2 = 0.0;
+                for (int k = 0; k < 3; ++k) {
+                    const double v = hi.pos[3 * j + k] - hi.pos[3 * i + k];
+                    r2 += v * v;
+                }
+                if (std::sqrt(r2) < rc) g.adj.push_back(static_cast<int>(j));
+            }
+            g.begin[i + 1] = static_cast<int64_t>(g.adj.size());
+        }
+        return g;
+    }
+    const int lat = d.lattice, nb = kBasisCount[lat];
+    const int reach = static_cast<int>(std::ceil(rc / d.a)) + 1;
+    std::vector<std::vector<StencilEntry>> stencil(nb);
+    for (int b = 0; b < nb; ++b)
+        for (int dz = -reach; dz <= reach; ++dz)
+            for (int dy = -reach; dy <= reach; ++dy)
+                for (int dx = -reach; dx <= reach; ++dx)
+                    for (int b2 = 0; b2 < nb; ++b2) {
+                        const int hx = 2 * dx + kBasisHalf[lat][b2][0] - kBasisHalf[lat][b][0];
+                        const int hy = 2 * dy + kBasisHalf[lat][b2][1] - kBasisHalf[lat][b][1];
+                        const int hz = 2 * dz + kBasisHalf[lat][b2][2] - kBasisHalf[lat][b][2];
+                        const double r = 0.5 * d.a * std::sqrt(double(hx * hx + hy * hy + hz * hz));
+                        if (r > 0.0 && r < rc) stencil[b].push_back({{dx, dy, dz}, b2, r});
+                    }
+    const int *L = hi.cells;
+    for (int64_t i = 0; i < hi.n; ++i) {
+        const int b = static_cast<int>(i % nb);
+        const int64_t cell = i / nb;
+        const int ix = static_cast<int>(cell % L[0]);
+        const int iy = static_cast<int>((cell / L[0]) % L[1]);
+        const int iz = static_cast<int>(cell / (int64_t(L[0]) * L[1]));
+        row.clear();
+        for (const StencilEntry &e : stencil[b]) {
+            const int jx = ((ix + e.dcell[0]) % L[0] + L[0]) % L[0];
+            const int jy = ((iy + e.dcell[1]) % L[1] + L[1]) % L[1];
+            const int jz = ((iz + e.dcell[2]) % L[2] + L[2]) % L[2];
+            const int64_t j = ((int64_t(jz) * L[1] + jy) * L[0] + jx) * nb + e.basis_to;
+            if (j != i) row.push_back(j);
+        }
+        std::sort(row.begin(), row.end());
+        row.erase(std::unique(row.begin(), row.end()), row.end());
+        for (int64_t j : row) g.adj.push_back(static_cast<int>(j));
+        g.begin[i + 1] = static_cast<int64_t>(g.adj.size());
+    }
+    return g;
+}
+
+bool proper(const ColourGraph &g, int64_t n, const std::vector<int> &col)
+{
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = g.begin[i]; k < g.begin[i + 1]; ++k)
+            if (col[g.adj[k]] == col[i]) return false;
     return true;
 }
 
@@ -164,6 +228,14 @@ void colour_instance(const tts_system_desc &d, HostInstance *hi)
     if (hi->nbr.empty()) {
         hi->ncolours = 1;
         return;
+    }
+    // the graph to colour: exchange neighbours, or every pair within colour_rc
+    ColourGraph g;
+    if (d.colour_rc > largest_cutoff(d)) {
+        g = pairs_within(d, *hi, d.colour_rc);
+    } else {
+        g.begin = hi->nbr_begin;
+        g.adj = hi->nbr;
     }
     if (d.lattice != TTS_LATTICE_CLUSTER) {
         const int nb = kBasisCount[d.lattice];
@@ -184,7 +256,7 @@ void colour_instance(const tts_system_desc &d, HostInstance *hi)
             else
                 rule[i] = b;
         }
-        if (proper(*hi, rule)) {
+        if (proper(g, n, rule)) {
             hi->colour = rule;
             hi->ncolours = d.lattice == TTS_LATTICE_SC ? (all_even ? 2 : 3) : 4;
             return;
@@ -194,8 +266,8 @@ void colour_instance(const tts_system_desc &d, HostInstance *hi)
     std::vector<int64_t> seen(n + 1, -1);
     int used = 0;
     for (int64_t i = 0; i < n; ++i) {
-        for (int64_t k = hi->nbr_begin[i]; k < hi->nbr_begin[i + 1]; ++k)
-            if (hi->nbr[k] < i) seen[hi->colour[hi->nbr[k]]] = i;
+        for (int64_t k = g.begin[i]; k < g.begin[i + 1]; ++k)
+            if (g.adj[k] < i) seen[hi->colour[g.adj[k]]] = i;
         int c = 0;
         while (seen[c] == i) ++c;
         hi->colour[i] = c;

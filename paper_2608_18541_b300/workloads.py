@@ -223,3 +223,24 @@ def switching_campaign(peaks, ds, reps, n=13, t_peak=500 * FS, t_cool=500 * FS, 
             "spatial": "uniform"}
     steps = int(round((t_peak + max(ds) * t_cool + t_tail) / dt))
     return s, bath, steps
+
+
+def three_temperature(n=10, gamma_scale=1.0, sample_every=25):
+    """Three-temperature relaxation of moving-lattice bcc Fe (paper Sec. III):
+    electrons set to a hot T_e by the caller (tts_set_ttm_state) on one
+    uniform cell without a source, lattice and spins starting at 300 K /
+    aligned; gamma_scale multiplies the electron-ion friction."""
+    s = bcc_fe(n, T=300.0, alpha=0.1, sample_every=sample_every)
+    lat = morse_fe_lattice(strain_amp=0.0, T_init=300.0)
+    lat["gamma_p"] *= gamma_scale
+    # the lattice warms to ~400-550 K: atoms may stray 0.7 A from their sites, and
+    # no two atoms within 3.5 + 1.4 A share a colour, so that no exchange pair
+    # (3.5 A) can form inside one colour class as they move
+    lat["skin"] = 1.4
+    s["colour_rc"] = 4.9
+    # gamma_e ten times the GdFeCo value: a one-cell electron reservoir then
+    # holds enough energy that the ions' stochastic kicks never drive it
+    # below zero (with 225 the reservoir of a 2000-atom box empties)
+    bath = {"cells": [1, 1, 1], "gamma_e": 2250.0, "C_l": 3.1e6, "G": 1.7e18, "kappa_e": 0.0, "T0": 300.0,
+            "source": "none", "spatial": "uniform"}
+    return s, bath, lat

@@ -57,3 +57,15 @@ def test_fcc_gdfeco_model():
     # every atom has its 12 nearest neighbours at a / sqrt(2) and no others
     counts = [len(o.neighbours(i)[0]) for i in range(o.n)]
     assert set(counts) == {12}
+
+
+def test_t90_of_a_closed_form_relaxation():
+    from paper_2608_18541_b300 import threetemp as TT
+    t = np.linspace(0.0, 10.0, 10001)
+    T = 300.0 + 500.0 * (1.0 - np.exp(-t / 1.5))
+    # exact: 1 - exp(-t/tau) = 0.9 * (1 - exp(-10/tau)) for the tail-mean final value
+    Tf = T[-1000:].mean()
+    frac = 0.9 * (Tf - 300.0) / 500.0
+    want = -1.5 * np.log(1.0 - frac)
+    assert abs(TT.t90(t, T) - want) < 2e-3
+    assert abs(TT.t90(t, 1000.0 - (T - 300.0)) - want) < 2e-3      # a falling curve
