@@ -1278,8 +1278,7 @@ PairConsts make_pair_consts(const EngineState *e, const StepParams &p, int hsel)
     k.Bz = host_splat(p.B[2]);
     k.one = host_splat(1.0);
     k.neg1 = host_splat(-1.0);
-    k.u_scale = host_splat(std::ldexp(1.0, -23));
-    k.u_off = host_splat(std::ldexp(1.0, -24));
+    k.u_off = host_splat(std::ldexp(1.0, -24) - 1.0);
     k.m2ln2 = host_splat(-2.0 * std::log(2.0));
     k.twopi = host_splat(2.0 * M_PI);
     k.negpi = host_splat(-M_PI);

@@ -126,7 +126,7 @@ struct PairConsts {
     f2 nx, ny, nz;     // anisotropy axis
     f2 Bx, By, Bz;     // applied field (tesla)
     f2 one, neg1;
-    f2 u_scale, u_off; // uniform = (k >> 9) * 2^-23 + 2^-24
+    f2 u_off;          // uniform = (1 + (k >> 9) 2^-23) + u_off, u_off = 2^-24 - 1 (exact)
     f2 m2ln2;          // -2 ln 2   (-2 ln u = -2 ln2 log2 u)
     f2 twopi, negpi;
     f2 s3, s5, s7;     // sine Taylor coefficients -1/6, 1/120, -1/5040
@@ -141,10 +141,12 @@ __device__ __forceinline__ void pair_noise(const u32x4 &ctrA, const u32x4 &ctrB,
 {
     const u32x4 rA = philox4x32_10(ctrA, rk);
     const u32x4 rB = philox4x32_10(ctrB, rk);
-    const f2 u0 = fma2(f2_make(float(rA.x >> 9), float(rB.x >> 9)), k.u_scale, k.u_off);
-    const f2 u1 = fma2(f2_make(float(rA.y >> 9), float(rB.y >> 9)), k.u_scale, k.u_off);
-    const f2 u2 = fma2(f2_make(float(rA.z >> 9), float(rB.z >> 9)), k.u_scale, k.u_off);
-    const f2 u3 = fma2(f2_make(float(rA.w >> 9), float(rB.w >> 9)), k.u_scale, k.u_off);
+    // (1 + m 2^-23) - (1 - 2^-24) = (2m + 1) 2^-24 exactly, m = x >> 9
+    auto one_m = [](uint32_t x) { return __uint_as_float(0x3F800000u | (x >> 9)); };
+    const f2 u0 = f2_make(one_m(rA.x), one_m(rB.x)) + k.u_off;
+    const f2 u1 = f2_make(one_m(rA.y), one_m(rB.y)) + k.u_off;
+    const f2 u2 = f2_make(one_m(rA.z), one_m(rB.z)) + k.u_off;
+    const f2 u3 = f2_make(one_m(rA.w), one_m(rB.w)) + k.u_off;
     // radius sqrt(l) = l rsqrt(l) with l = -2 ln u = -2 ln2 log2 u
     const f2 l0 = f2_map<lg2_approx>(u0) * k.m2ln2;
     const f2 l2 = f2_map<lg2_approx>(u2) * k.m2ln2;
