@@ -199,6 +199,7 @@ struct PairArgs {
     FastDiv dLx, dLy, dLz;
     int shx, shy, shz;           // >= 0: L_k / n_k = 2^sh, c_k = k >> sh
     SweepCtl sw;                 // merged sweep: leading / trailing colour-0 pass
+    int pf_planes;               // L2 prefetch distance in z planes (0: none)
 };
 
 struct Pair4 {
@@ -357,6 +358,22 @@ __device__ __forceinline__ void pair_block(const PairArgs &a, int colour, int hs
     const uint32_t kx = (bx - yb * a.nkx) * blockDim.x + threadIdx.x;
     const uint32_t y2 = yb * blockDim.y + threadIdx.y;
     const uint32_t hx = a.hx, Ly2 = a.Ly2, Lz = a.Lz;
+    // One thread asks the copy engine to bring this block's rows of both
+    // colours at plane z + pf_planes into L2 (bulk prefetch, no registers, no
+    // completion to wait for): the blocks that will read them -- the same rows
+    // a few planes on, and their z neighbours -- then hit L2 instead of HBM.
+    if (a.pf_planes > 0 && threadIdx.x == 0 && threadIdx.y == 0 && z + a.pf_planes < Lz) {
+        const uint32_t zf = z + a.pf_planes, y0 = yb * blockDim.y, kx0 = (bx - yb * a.nkx) * blockDim.x;
+        const uint32_t rows = min(blockDim.y, Ly2 - y0), cols = min(blockDim.x, hx - kx0);
+        const ulonglong2 *ib = a.S + int64_t(inst) * a.n_inst_sites;
+        for (uint32_t r = 0; r < rows; ++r) {
+            const uint32_t q = (zf * Ly2 + y0 + r) * hx + kx0;
+            bulk_prefetch_l2(ib + q, cols * 16u);                           // colour 0, lo plane
+            bulk_prefetch_l2(ib + a.npair + q, cols * 16u);                 // colour 0, hi plane
+            bulk_prefetch_l2(ib + a.nhalf + q, cols * 16u);                 // colour 1, lo plane
+            bulk_prefetch_l2(ib + a.nhalf + a.npair + q, cols * 16u);       // colour 1, hi plane
+        }
+    }
     if (y2 >= Ly2 || kx >= hx) return;
     const PairSite p = make_site(a, inst, z, y2, kx, colour);
     f2 g1{0}, g2{0}, g3{0};
@@ -1678,6 +1695,9 @@ PairArgs pair_args(const EngineState *e, const StepParams &p, const DevBuffers &
     a.dLx = make_fastdiv(e->shape[0]);
     a.dLy = make_fastdiv(e->shape[1]);
     a.dLz = make_fastdiv(e->shape[2]);
+    // two planes ahead: measured 5 % faster than none on the 128^3 x 4 benchmark
+    // (one to four planes all gave the same; a wave of blocks ahead, 37 planes, 0.6 %)
+    a.pf_planes = 2;
     int *sh[3] = {&a.shx, &a.shy, &a.shz};
     for (int k = 0; k < 3; ++k) {
         *sh[k] = -1;
