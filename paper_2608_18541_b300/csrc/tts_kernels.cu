@@ -574,9 +574,21 @@ cudaError_t launch_calibrate(const CalibJob *jobs_dev, const double *cand_dev, d
 }
 
 // ---------------------------------------------------------------------------
+// Block size of the per-cell FP64 kernels (sigma table, TTM).  Their work is
+// FP64 divisions, square roots and exponentials at about two FP64 FMAs a clock
+// a SM, so a few thousand cells in 256-thread blocks would occupy a tenth of
+// the SMs: take the largest power of two in [32, 256] that still gives a
+// block to each of the 148 SMs.  Each thread computes the same cell either way.
+static int cell_block(int64_t n)
+{
+    int bs = 256;
+    while (bs > 32 && (n + bs - 1) / bs < 148) bs >>= 1;
+    return bs;
+}
+
 cudaError_t launch_sigma(const StepParams &p, const DevBuffers &b, int ncells, int precision, cudaStream_t st)
 {
-    const int bs = 128, gs = (ncells + bs - 1) / bs;
+    const int bs = cell_block(ncells), gs = (ncells + bs - 1) / bs;
     if (precision == 64)
         sigma_kernel<double><<<gs, bs, 0, st>>>(p, b.Te, static_cast<double *>(b.sigma), ncells);
     else
@@ -611,25 +623,24 @@ cudaError_t launch_set_target(const DevBuffers &b, int64_t n, cudaStream_t st)
 cudaError_t launch_ttm(const StepParams &p, const DevBuffers &b, const TtmParams &tp, int n_instances,
                        cudaStream_t st, int precision, int inc_step)
 {
+    const int n = p.ncells_total, bs = cell_block(n), gs = (n + bs - 1) / bs;
     if (b.cell_inst && tp.source == TTS_SOURCE_STEP_PROFILE) {
-        const int n = p.ncells_total;
         if (precision == 64)
-            ttm_profile_kernel<double><<<(n + 255) / 256, 256, 0, st>>>(p, b, tp, b.cell_inst, n);
+            ttm_profile_kernel<double><<<gs, bs, 0, st>>>(p, b, tp, b.cell_inst, n);
         else
-            ttm_profile_kernel<float><<<(n + 255) / 256, 256, 0, st>>>(p, b, tp, b.cell_inst, n);
+            ttm_profile_kernel<float><<<gs, bs, 0, st>>>(p, b, tp, b.cell_inst, n);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess || !inc_step) return e;
         return launch_step_inc(b, st);
     }
     if (b.cell_inst && p.ttm_one_substep) {
-        const int n = p.ncells_total;
-        ttm_increment_kernel<<<(n + 255) / 256, 256, 0, st>>>(p, b, tp, b.cell_inst, n);
+        ttm_increment_kernel<<<gs, bs, 0, st>>>(p, b, tp, b.cell_inst, n);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (precision == 64)
-            ttm_apply_kernel<double><<<(n + 255) / 256, 256, 0, st>>>(p, b, tp, n, inc_step);
+            ttm_apply_kernel<double><<<gs, bs, 0, st>>>(p, b, tp, n, inc_step);
         else
-            ttm_apply_kernel<float><<<(n + 255) / 256, 256, 0, st>>>(p, b, tp, n, inc_step);
+            ttm_apply_kernel<float><<<gs, bs, 0, st>>>(p, b, tp, n, inc_step);
         return cudaGetLastError();
     }
     ttm_kernel<<<n_instances, 256, 0, st>>>(p, b, tp);
