@@ -218,6 +218,8 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     sysd, ttm, desc = _workload(args.workload)
+    sample_every = args.chunk if args.sample_every < 0 else args.sample_every
+    sysd = dict(sysd, sample_every=sample_every)
     import oracle as O
     inst0 = dict(sysd)
     if inst0.get("instances"):
@@ -234,7 +236,8 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": "spin-steps/s", "value": v, "unit": "spin-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": desc, "sample": "one realisation, one dt per step"},
+        "data": "synthetic", "config": {"workload": desc, "sample_every": sample_every,
+                                              "sample": "one realisation, one dt per step"},
         "cpu_baseline": {"value": v, "unit": "spin-steps/s", "cores": 1, "kind": "oracle",
                          "sample": "1 of %d realisations (%d spins), %d steps of dt" % (
                              len(sysd.get("instances") or [0]), o.n, args.steps)},
@@ -250,6 +253,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--chunk", type=int, default=100, help="time steps per benchmark step")
+    ap.add_argument("--sample-every", type=int, default=-1,
+                    help="observable sampling interval in time steps (default: once per chunk; 0: off)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gdfeco_128x4")
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
@@ -280,6 +285,10 @@ def main():
     if not os.path.exists(P.LIB_PATH):
         B.build()
     sysd, ttm, desc = _workload(args.workload)
+    # the per-sample reductions (magnetisation per sublattice, energies, spin
+    # temperature, mean T_e and T_l) are part of the timed path
+    sample_every = args.chunk if args.sample_every < 0 else args.sample_every
+    sysd = dict(sysd, sample_every=sample_every)
     n_inst_local = len(sysd.get("instances") or [0])
     stream = torch.cuda.current_stream()
     g = P.System(sysd, ttm, precision=args.precision, engine=args.engine, stream=stream.cuda_stream,
@@ -390,6 +399,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
         "config": {"workload": desc, "spins_per_gpu": spins, "dt_per_step": args.chunk,
+                   "sample_every": sample_every,
                    "engine": engine, "l2": "state and tables exceed L2 (126 MB) per step" if spins * 16 > 126e6
                    else "working set may fit L2", "parallelism": "instances sharded, dp%d" % world},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
