@@ -1828,7 +1828,7 @@ cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuf
     }
     if (err == cudaSuccess && ev1) err = cudaEventRecord(ev1, st);
     bool partials = false;
-    if (err == cudaSuccess && p.sample_every > 0) {
+    if (err == cudaSuccess && p.sample_every > 0 && !p.obs_skip) {
         if (e->pair) {
             // observables straight from the pair layout (sampling steps only)
             err = engine_obs_partials(e, p, b, 0, st);

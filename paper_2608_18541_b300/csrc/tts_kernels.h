@@ -26,6 +26,8 @@ struct StepParams {
     int sigma_per_step;      // the noise table is rebuilt by its own kernel every step
     int lattice_on;          // observables of a moving lattice (sampled per lattice step)
     int merged;              // merged (leapfrog) sweep (engines read it from here)
+    int obs_skip;            // host-side: record this step without its observable kernels
+                             // (a step the host knows does not sample)
     int64_t *lstep;          // lattice step counter (moving lattice)
     double *lat_partial;     // per observable block: kinetic and pair energy (moving lattice)
 };

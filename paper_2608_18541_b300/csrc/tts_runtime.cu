@@ -15,6 +15,7 @@
 #include "tts_engines.h"
 #include "tts_internal.h"
 #include "tts_kernels.h"
+#include "tts_schedule.h"
 #include "tts_system.h"
 
 using namespace tts;
@@ -237,12 +238,13 @@ SweepCtl sweep_ctl(const tts_system *s, int pass, int npass)
     return w;
 }
 
-cudaError_t record_step(tts_system *s, cudaStream_t c, int *kernels, cudaEvent_t ev0, cudaEvent_t ev1)
+cudaError_t record_step(tts_system *s, cudaStream_t c, int *kernels, cudaEvent_t ev0, cudaEvent_t ev1, bool obs)
 {
     *kernels = 0;
     if (s->lat) return lattice_record_step(s, c, kernels, ev0, ev1);
+    StepParams p = s->p;
+    p.obs_skip = obs ? 0 : 1;
     if (s->eng) {
-        StepParams p = s->p;
         p.merged = s->merged ? 1 : 0;
         return engine_record_step(s->eng, p, s->b, s->tp, s->ttm_active, c, kernels, ev0, ev1);
     }
@@ -261,18 +263,25 @@ cudaError_t record_step(tts_system *s, cudaStream_t c, int *kernels, cudaEvent_t
         ++*kernels;
     }
     if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, c);
-    e = (e == cudaSuccess) ? step_tail(s->p, s->b, s->tp, s->ttm_active, s->n_inst, s->precision, s->obs_blocks, c, kernels)
+    e = (e == cudaSuccess) ? step_tail(p, s->b, s->tp, s->ttm_active, s->n_inst, s->precision, s->obs_blocks, c, kernels)
                            : e;
     return e;
 }
 
-int capture_steps(tts_system *s, int nsteps, cudaGraphExec_t *out, int *kernels_per_step)
+// Capture nsteps steps into one graph.  obs: 0 = every step without its
+// observable kernels, 1 = every step with them, 2 = only the last step with
+// them.  *kernels_out = kernels per replay.
+int capture_steps(tts_system *s, int nsteps, int obs, cudaGraphExec_t *out, int *kernels_out)
 {
     cudaStream_t c = s->capture;
     TTS_CUDA(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal), "begin capture");
-    int kernels = 0;
+    int total = 0;
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < nsteps && e == cudaSuccess; ++i) e = record_step(s, c, &kernels, nullptr, nullptr);
+    for (int i = 0; i < nsteps && e == cudaSuccess; ++i) {
+        int kernels = 0;
+        e = record_step(s, c, &kernels, nullptr, nullptr, obs == 1 || (obs == 2 && i == nsteps - 1));
+        total += kernels;
+    }
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c, &g);
     if (e != cudaSuccess) {
@@ -283,24 +292,35 @@ int capture_steps(tts_system *s, int nsteps, cudaGraphExec_t *out, int *kernels_
     e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "instantiate step graph");
-    *kernels_per_step = kernels;
+    *kernels_out = total;
     return TTS_OK;
 }
 
+// Longest sampling interval captured as one graph (about five kernels a step).
+constexpr int kMaxCycleSteps = 256;
+
 int build_graph(tts_system *s)
 {
-    for (cudaGraphExec_t *g : {&s->graph, &s->graph_multi})
+    for (cudaGraphExec_t *g : {&s->graph, &s->graph_multi, &s->graph_plain, &s->graph_cycle})
         if (*g) {
             cudaGraphExecDestroy(*g);
             *g = nullptr;
         }
     // a moving lattice has ~100 kernels per step: fewer steps per graph
     s->graph_steps = s->lat ? 4 : 16;
-    int k1 = 0, km = 0;
-    int rc = capture_steps(s, 1, &s->graph, &k1);
-    if (!rc) rc = capture_steps(s, s->graph_steps, &s->graph_multi, &km);
+    // While sampling, graphs follow the sampling phase (tts_schedule.h); a
+    // moving lattice samples on its lattice clock and keeps the observable
+    // kernels in every step.
+    s->phased = !s->lat && s->p.sample_every > 0;
+    s->cycle_steps = 0;
+    int rc = capture_steps(s, 1, 1, &s->graph, &s->kernels_graph);
+    if (!rc) rc = capture_steps(s, s->graph_steps, s->phased ? 0 : 1, &s->graph_multi, &s->kernels_multi);
+    if (!rc && s->phased) rc = capture_steps(s, 1, 0, &s->graph_plain, &s->kernels_plain);
+    if (!rc && s->phased && s->p.sample_every >= 2 && s->p.sample_every <= kMaxCycleSteps) {
+        rc = capture_steps(s, s->p.sample_every, 2, &s->graph_cycle, &s->kernels_cycle);
+        if (!rc) s->cycle_steps = s->p.sample_every;
+    }
     if (rc) return rc;
-    s->kernels_per_step = k1;
     s->dirty = false;
     return TTS_OK;
 }
@@ -320,7 +340,7 @@ void drop_profile_events(tts_system *s)
 cudaError_t tts::step_tail(const StepParams &p, const DevBuffers &b, const TtmParams &tp, bool ttm_active, int n_inst,
                            int precision, int obs_blocks, cudaStream_t st, int *kernels, bool partials_done)
 {
-    const bool sampling = p.sample_every > 0;
+    const bool sampling = p.sample_every > 0 && !p.obs_skip;
     const bool fold = ttm_active && p.ttm_one_substep && !sampling;
     cudaError_t e = cudaSuccess;
     if (ttm_active) {
@@ -430,8 +450,8 @@ int tts_destroy(tts_system *s)
 {
     if (!s) return TTS_OK;
     cudaStreamSynchronize(s->stream);
-    if (s->graph) cudaGraphExecDestroy(s->graph);
-    if (s->graph_multi) cudaGraphExecDestroy(s->graph_multi);
+    for (cudaGraphExec_t g : {s->graph, s->graph_multi, s->graph_plain, s->graph_cycle})
+        if (g) cudaGraphExecDestroy(g);
     drop_profile_events(s);
     if (s->eng) engine_destroy(s->eng);
     if (s->lat) lattice_destroy(s->lat);
@@ -922,6 +942,9 @@ int tts_step(tts_system *s, int64_t nsteps)
     if (nsteps == 0) return TTS_OK;
     if (s->merged && !s->eng && !s->merged_uniform)
         return fail(TTS_ERR_UNSUPPORTED, "the merged sweep on the general engine needs the same colour count in every instance");
+    // every path below advances the device counter by nsteps
+    const int64_t step0 = s->host_step;
+    s->host_step += nsteps;
     if (s->merged && !(s->eng && engine_multi_step(s->eng))) {
         // the last step of this call closes the merged sweep
         TTS_CUDA(launch_set_target(s->b, nsteps, s->stream), "sweep target");
@@ -954,7 +977,7 @@ int tts_step(tts_system *s, int64_t nsteps)
             s->prof_events.push_back(ev[1]);
             s->prof_pair_steps.push_back(1);
             int kernels = 0;
-            cudaError_t e = record_step(s, s->stream, &kernels, ev[0], ev[1]);
+            cudaError_t e = record_step(s, s->stream, &kernels, ev[0], ev[1], true);
             if (e != cudaSuccess) return cuda_fail(e, "profiled step");
             s->launches += kernels;
         }
@@ -964,11 +987,37 @@ int tts_step(tts_system *s, int64_t nsteps)
         int rc = build_graph(s);
         if (rc) return rc;
     }
-    int64_t left = nsteps;
-    for (; left >= s->graph_steps; left -= s->graph_steps)
-        TTS_CUDA(cudaGraphLaunch(s->graph_multi, s->stream), "launch step graph");
-    for (; left > 0; --left) TTS_CUDA(cudaGraphLaunch(s->graph, s->stream), "launch step graph");
-    s->launches += nsteps * s->kernels_per_step;
+    if (!s->phased) {
+        int64_t left = nsteps;
+        for (; left >= s->graph_steps; left -= s->graph_steps) {
+            TTS_CUDA(cudaGraphLaunch(s->graph_multi, s->stream), "launch step graph");
+            s->launches += s->kernels_multi;
+        }
+        for (; left > 0; --left) {
+            TTS_CUDA(cudaGraphLaunch(s->graph, s->stream), "launch step graph");
+            s->launches += s->kernels_graph;
+        }
+        return TTS_OK;
+    }
+    cudaError_t err = cudaSuccess;
+    schedule_steps(step0, nsteps, s->p.sample_every, s->graph_steps, s->cycle_steps, [&](StepGraph g, int64_t) {
+        if (err != cudaSuccess) return;
+        cudaGraphExec_t x = s->graph;
+        int k = s->kernels_graph;
+        if (g == StepGraph::Cycle) {
+            x = s->graph_cycle;
+            k = s->kernels_cycle;
+        } else if (g == StepGraph::PlainRun) {
+            x = s->graph_multi;
+            k = s->kernels_multi;
+        } else if (g == StepGraph::Plain) {
+            x = s->graph_plain;
+            k = s->kernels_plain;
+        }
+        err = cudaGraphLaunch(x, s->stream);
+        if (err == cudaSuccess) s->launches += k;
+    });
+    if (err != cudaSuccess) return cuda_fail(err, "launch step graph");
     return TTS_OK;
 }
 
@@ -1310,6 +1359,7 @@ int tts_set_step(tts_system *s, int64_t step)
     TTS_CUDA(cudaStreamSynchronize(s->stream), "set step");
     TTS_CUDA(cudaMemcpy(s->b.step, &step, sizeof(int64_t), cudaMemcpyHostToDevice), "write step");
     TTS_CUDA(cudaMemset(s->b.open, 0, sizeof(int)), "reset sweep state");
+    s->host_step = step;
     return TTS_OK;
 }
 
@@ -1393,6 +1443,7 @@ int tts_set_state(tts_system *s, const void *buf, size_t nbytes)
     o += sizeof h;
     TTS_CUDA(cudaMemcpy(s->b.step, &h[7], sizeof(int64_t), cudaMemcpyHostToDevice), "write step");
     TTS_CUDA(cudaMemset(s->b.open, 0, sizeof(int)), "reset sweep state");
+    s->host_step = h[7];
     for (void *arr : {s->b.sx, s->b.sy, s->b.sz}) {
         TTS_CUDA(cudaMemcpy(arr, o, size_t(s->n_total) * s->rsize, cudaMemcpyHostToDevice), "write spins");
         o += size_t(s->n_total) * s->rsize;

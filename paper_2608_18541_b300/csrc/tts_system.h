@@ -80,10 +80,15 @@ struct tts_system {
     int obs_capacity = 1024;
     tts::DevBuffers b;
     tts::StepParams p{};
-    cudaGraphExec_t graph = nullptr;        // one step
-    cudaGraphExec_t graph_multi = nullptr;  // graph_steps steps
+    cudaGraphExec_t graph = nullptr;        // one step (with its observable kernels, if sampling)
+    cudaGraphExec_t graph_multi = nullptr;  // graph_steps steps (without them, if sampling)
+    cudaGraphExec_t graph_plain = nullptr;  // sampling only: one step without them
+    cudaGraphExec_t graph_cycle = nullptr;  // sampling only: one sampling interval, them in its last step
     int graph_steps = 16;
-    int kernels_per_step = 0;
+    int cycle_steps = 0;                    // steps of graph_cycle (0: none)
+    int kernels_graph = 0, kernels_multi = 0, kernels_plain = 0, kernels_cycle = 0;   // per replay
+    bool phased = false;                    // the graphs follow the sampling phase (above)
+    int64_t host_step = 0;                  // host copy of the device step counter
     int64_t launches = 0;
     bool dirty = true;
     tts::EngineState *eng = nullptr;                     // fast-engine state, if any
