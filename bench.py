@@ -5,7 +5,10 @@ Workload (default): GdFeCo on a simple-cubic 128^3 lattice (2,097,152 spins)
 x 4 realisations, random 25 % Gd, constant nearest-neighbour exchange, a
 16^3 TTM grid with a Gaussian laser spot (sigma 40 A) calibrated to a 2000 K
 peak, FP32 spins with FP64 TTM, sigma-table and reductions, dt = 0.1 fs.
-One benchmark step = `--chunk` time steps of every spin of every realisation.
+One benchmark step = `--chunk` time steps of every spin of every realisation,
+with the observables (per-sublattice magnetisation, energies, spin
+temperature, mean T_e and T_l, FP64) sampled every `--sample-every` steps
+(default: once per chunk) inside the timed region.
 
 Metric: spin-steps/s (one spin advanced by one full dt) over all GPUs, with
 the fraction of the HBM roofline of the dominant kernel.  The reference arm
