@@ -24,8 +24,10 @@ def contiguous_shards(costs, world):
         else:
             target = total * (r + 1) / world
             end = start
-            # extend while the running sum stays closer to the target
-            while end < n - (world - 1 - r) and acc + costs[end] - target <= target - acc:
+            # take at least one instance while every later rank can still
+            # get one, then extend while the running sum stays closer to the
+            # target
+            while end < n - (world - 1 - r) and (end == start or acc + costs[end] - target <= target - acc):
                 acc += costs[end]
                 end += 1
         out.append((start, end - start))
