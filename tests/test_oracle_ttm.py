@@ -76,7 +76,7 @@ def test_peak_calibration_hits_target():
         for _ in range(int(round((3 + 10) * fwhm / 2.3548 / (0.1 * FS)))):
             o.step(1)
             mx = max(mx, o.ttm()[0][0])
-        assert abs(mx - peak) < 1e-6
+        assert abs(mx - peak) < 1e-9
 
 
 def test_diffusion_eigenmode_decay():
