@@ -63,60 +63,71 @@ _SPATIAL = {"uniform": 0, "xy_gauss": 1, "z_exp": 2}
 def lib():
     global _LIB
     if _LIB is None:
-        L = C.CDLL(_build.build())
-        P = C.POINTER
-        d, i64, u32 = C.c_double, C.c_int64, C.c_uint32
-        L.orc_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
-        L.orc_uniform.argtypes = [u32]
-        L.orc_uniform.restype = d
-        L.orc_gauss3.argtypes = [P(u32), P(d)]
-        L.orc_bethe_slater.argtypes = [d, d, d, d]
-        L.orc_bethe_slater.restype = d
-        L.orc_bethe_slater_deriv.argtypes = [d, d, d, d]
-        L.orc_bethe_slater_deriv.restype = d
-        L.orc_rederive_exchange.argtypes = [d, P(d), P(d), P(d)]
-        L.orc_flow.argtypes = [P(d), P(d), d, d]
-        L.orc_create.argtypes = [P(_Params), C.c_char_p, C.c_int]
-        L.orc_create.restype = C.c_void_p
-        L.orc_free.argtypes = [C.c_void_p]
-        L.orc_set_ttm.argtypes = [C.c_void_p, P(_Ttm), C.c_char_p, C.c_int]
-        L.orc_step.argtypes = [C.c_void_p, i64]
-        for name in ("orc_natoms", "orc_ncolours", "orc_ttm_substeps", "orc_ttm_ncells"):
-            getattr(L, name).argtypes = [C.c_void_p]
-        L.orc_stepcount.argtypes = [C.c_void_p]
-        L.orc_stepcount.restype = i64
-        L.orc_set_stepcount.argtypes = [C.c_void_p, i64]
-        L.orc_get_spins.argtypes = [C.c_void_p, P(d)]
-        L.orc_set_spins.argtypes = [C.c_void_p, P(d)]
-        L.orc_get_species.argtypes = [C.c_void_p, P(C.c_int)]
-        L.orc_get_colours.argtypes = [C.c_void_p, P(C.c_int)]
-        L.orc_get_positions.argtypes = [C.c_void_p, P(d)]
-        L.orc_neighbour_count.argtypes = [C.c_void_p, C.c_int]
-        L.orc_get_neighbours.argtypes = [C.c_void_p, C.c_int, P(C.c_int), P(d)]
-        L.orc_field.argtypes = [C.c_void_p, C.c_int, P(d)]
-        L.orc_observe.argtypes = [C.c_void_p, P(d)]
-        L.orc_nsamples.argtypes = [C.c_void_p]
-        L.orc_nsamples.restype = i64
-        L.orc_get_samples.argtypes = [C.c_void_p, P(d)]
-        L.orc_ttm_P0.argtypes = [C.c_void_p]
-        L.orc_ttm_P0.restype = d
-        L.orc_ttm_get.argtypes = [C.c_void_p, P(d), P(d)]
-        L.orc_ttm_set.argtypes = [C.c_void_p, P(d), P(d)]
-        L.orc_ttm_source_energy.argtypes = [C.c_void_p]
-        L.orc_ttm_source_energy.restype = d
-        L.orc_atom_cell.argtypes = [C.c_void_p, C.c_int]
-        L.orc_set_lattice.argtypes = [C.c_void_p, P(_Lattice), C.c_char_p, C.c_int]
-        L.orc_lattice_step.argtypes = [C.c_void_p, i64]
-        L.orc_lattice_stepcount.argtypes = [C.c_void_p]
-        L.orc_lattice_stepcount.restype = i64
-        for name in ("orc_get_velocities", "orc_set_positions", "orc_set_velocities", "orc_get_forces"):
-            getattr(L, name).argtypes = [C.c_void_p, P(d)]
-        L.orc_lattice_energy.argtypes = [C.c_void_p, P(d), P(d)]
-        L.orc_colour_violations.argtypes = [C.c_void_p]
-        L.orc_ion_energy_to_electrons.argtypes = [C.c_void_p]
-        L.orc_ion_energy_to_electrons.restype = d
-        _LIB = L
+        _LIB = _load(_build.build())
     return _LIB
+
+
+def load_variant(path):
+    """ctypes view of an altered oracle build (oracle.build.build_variant),
+    for tests that show a pin fails on a planted mistake; pass it to Oracle
+    as `library=`."""
+    return _load(path)
+
+
+def _load(path):
+    L = C.CDLL(path)
+    P = C.POINTER
+    d, i64, u32 = C.c_double, C.c_int64, C.c_uint32
+    L.orc_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
+    L.orc_uniform.argtypes = [u32]
+    L.orc_uniform.restype = d
+    L.orc_gauss3.argtypes = [P(u32), P(d)]
+    L.orc_bethe_slater.argtypes = [d, d, d, d]
+    L.orc_bethe_slater.restype = d
+    L.orc_bethe_slater_deriv.argtypes = [d, d, d, d]
+    L.orc_bethe_slater_deriv.restype = d
+    L.orc_rederive_exchange.argtypes = [d, P(d), P(d), P(d)]
+    L.orc_flow.argtypes = [P(d), P(d), d, d]
+    L.orc_create.argtypes = [P(_Params), C.c_char_p, C.c_int]
+    L.orc_create.restype = C.c_void_p
+    L.orc_free.argtypes = [C.c_void_p]
+    L.orc_set_ttm.argtypes = [C.c_void_p, P(_Ttm), C.c_char_p, C.c_int]
+    L.orc_step.argtypes = [C.c_void_p, i64]
+    for name in ("orc_natoms", "orc_ncolours", "orc_ttm_substeps", "orc_ttm_ncells"):
+        getattr(L, name).argtypes = [C.c_void_p]
+    L.orc_stepcount.argtypes = [C.c_void_p]
+    L.orc_stepcount.restype = i64
+    L.orc_set_stepcount.argtypes = [C.c_void_p, i64]
+    L.orc_get_spins.argtypes = [C.c_void_p, P(d)]
+    L.orc_set_spins.argtypes = [C.c_void_p, P(d)]
+    L.orc_get_species.argtypes = [C.c_void_p, P(C.c_int)]
+    L.orc_get_colours.argtypes = [C.c_void_p, P(C.c_int)]
+    L.orc_get_positions.argtypes = [C.c_void_p, P(d)]
+    L.orc_neighbour_count.argtypes = [C.c_void_p, C.c_int]
+    L.orc_get_neighbours.argtypes = [C.c_void_p, C.c_int, P(C.c_int), P(d)]
+    L.orc_field.argtypes = [C.c_void_p, C.c_int, P(d)]
+    L.orc_observe.argtypes = [C.c_void_p, P(d)]
+    L.orc_nsamples.argtypes = [C.c_void_p]
+    L.orc_nsamples.restype = i64
+    L.orc_get_samples.argtypes = [C.c_void_p, P(d)]
+    L.orc_ttm_P0.argtypes = [C.c_void_p]
+    L.orc_ttm_P0.restype = d
+    L.orc_ttm_get.argtypes = [C.c_void_p, P(d), P(d)]
+    L.orc_ttm_set.argtypes = [C.c_void_p, P(d), P(d)]
+    L.orc_ttm_source_energy.argtypes = [C.c_void_p]
+    L.orc_ttm_source_energy.restype = d
+    L.orc_atom_cell.argtypes = [C.c_void_p, C.c_int]
+    L.orc_set_lattice.argtypes = [C.c_void_p, P(_Lattice), C.c_char_p, C.c_int]
+    L.orc_lattice_step.argtypes = [C.c_void_p, i64]
+    L.orc_lattice_stepcount.argtypes = [C.c_void_p]
+    L.orc_lattice_stepcount.restype = i64
+    for name in ("orc_get_velocities", "orc_set_positions", "orc_set_velocities", "orc_get_forces"):
+        getattr(L, name).argtypes = [C.c_void_p, P(d)]
+    L.orc_lattice_energy.argtypes = [C.c_void_p, P(d), P(d)]
+    L.orc_colour_violations.argtypes = [C.c_void_p]
+    L.orc_ion_energy_to_electrons.argtypes = [C.c_void_p]
+    L.orc_ion_energy_to_electrons.restype = d
+    return L
 
 
 def _dptr(a):
@@ -253,8 +264,9 @@ class Oracle:
     index: the entry of sysd["instances"] that gives its size, composition and
     pulse (defaults to `instance`)."""
 
-    def __init__(self, sysd, ttm=None, instance=0, noise_mu_power=0.5, index=None, lattice=None):
-        L = lib()
+    def __init__(self, sysd, ttm=None, instance=0, noise_mu_power=0.5, index=None, lattice=None,
+                 library=None):
+        self._L = L = library if library is not None else lib()
         index = instance if index is None else index
         p, self._keep = _fill_params(sysd, instance, index, noise_mu_power)
         err = C.create_string_buffer(256)
@@ -277,51 +289,51 @@ class Oracle:
                 raise ValueError(err.value.decode())
 
     def __del__(self):
-        if getattr(self, "_h", None) and _LIB is not None:
-            _LIB.orc_free(self._h)
+        if getattr(self, "_h", None) and getattr(self, "_L", None) is not None:
+            self._L.orc_free(self._h)
             self._h = None
 
     def step(self, n):
-        lib().orc_step(self._h, int(n))
+        self._L.orc_step(self._h, int(n))
 
     @property
     def ncolours(self):
-        return lib().orc_ncolours(self._h)
+        return self._L.orc_ncolours(self._h)
 
     @property
     def stepcount(self):
-        return lib().orc_stepcount(self._h)
+        return self._L.orc_stepcount(self._h)
 
     @stepcount.setter
     def stepcount(self, n):
-        lib().orc_set_stepcount(self._h, int(n))
+        self._L.orc_set_stepcount(self._h, int(n))
 
     def spins(self):
         out = np.empty((self.n, 3), dtype=np.float64)
-        lib().orc_get_spins(self._h, _dptr(out))
+        self._L.orc_get_spins(self._h, _dptr(out))
         return out
 
     def set_spins(self, s):
         s = np.ascontiguousarray(s, dtype=np.float64).reshape(self.n, 3)
-        lib().orc_set_spins(self._h, _dptr(s))
+        self._L.orc_set_spins(self._h, _dptr(s))
 
     def species(self):
         out = np.empty(self.n, dtype=np.int32)
-        lib().orc_get_species(self._h, _iptr(out))
+        self._L.orc_get_species(self._h, _iptr(out))
         return out
 
     def colours(self):
         out = np.empty(self.n, dtype=np.int32)
-        lib().orc_get_colours(self._h, _iptr(out))
+        self._L.orc_get_colours(self._h, _iptr(out))
         return out
 
     def positions(self):
         out = np.empty((self.n, 3), dtype=np.float64)
-        lib().orc_get_positions(self._h, _dptr(out))
+        self._L.orc_get_positions(self._h, _dptr(out))
         return out
 
     def neighbours(self, i):
-        L = lib()
+        L = self._L
         m = L.orc_neighbour_count(self._h, int(i))
         j = np.empty(m, dtype=np.int32)
         J = np.empty(m, dtype=np.float64)
@@ -330,16 +342,16 @@ class Oracle:
 
     def field(self, i):
         out = np.empty(3, dtype=np.float64)
-        lib().orc_field(self._h, int(i), _dptr(out))
+        self._L.orc_field(self._h, int(i), _dptr(out))
         return out
 
     def observe(self):
         out = np.empty(NOBS, dtype=np.float64)
-        lib().orc_observe(self._h, _dptr(out))
+        self._L.orc_observe(self._h, _dptr(out))
         return out
 
     def samples(self):
-        L = lib()
+        L = self._L
         m = L.orc_nsamples(self._h)
         out = np.empty((m, NOBS), dtype=np.float64)
         if m:
@@ -348,14 +360,14 @@ class Oracle:
 
     @property
     def P0(self):
-        return lib().orc_ttm_P0(self._h)
+        return self._L.orc_ttm_P0(self._h)
 
     @property
     def ttm_substeps(self):
-        return lib().orc_ttm_substeps(self._h)
+        return self._L.orc_ttm_substeps(self._h)
 
     def ttm(self):
-        L = lib()
+        L = self._L
         nc = L.orc_ttm_ncells(self._h)
         Te = np.empty(nc)
         Tl = np.empty(nc)
@@ -366,44 +378,44 @@ class Oracle:
     def set_ttm_state(self, Te, Tl):
         Te = np.ascontiguousarray(Te, dtype=np.float64)
         Tl = np.ascontiguousarray(Tl, dtype=np.float64)
-        lib().orc_ttm_set(self._h, _dptr(Te), _dptr(Tl))
+        self._L.orc_ttm_set(self._h, _dptr(Te), _dptr(Tl))
 
     @property
     def source_energy(self):
-        return lib().orc_ttm_source_energy(self._h)
+        return self._L.orc_ttm_source_energy(self._h)
 
     def atom_cell(self, i):
-        return lib().orc_atom_cell(self._h, int(i))
+        return self._L.orc_atom_cell(self._h, int(i))
 
     # -- moving lattice -------------------------------------------------------
     def lattice_step(self, n):
-        lib().orc_lattice_step(self._h, int(n))
+        self._L.orc_lattice_step(self._h, int(n))
 
     @property
     def lattice_stepcount(self):
-        return lib().orc_lattice_stepcount(self._h)
+        return self._L.orc_lattice_stepcount(self._h)
 
     def velocities(self):
         out = np.empty((self.n, 3))
-        lib().orc_get_velocities(self._h, _dptr(out))
+        self._L.orc_get_velocities(self._h, _dptr(out))
         return out
 
     def set_velocities(self, v):
         v = np.ascontiguousarray(v, dtype=np.float64).reshape(self.n, 3)
-        lib().orc_set_velocities(self._h, _dptr(v))
+        self._L.orc_set_velocities(self._h, _dptr(v))
 
     def set_positions(self, x):
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(self.n, 3)
-        lib().orc_set_positions(self._h, _dptr(x))
+        self._L.orc_set_positions(self._h, _dptr(x))
 
     def forces(self):
         out = np.empty((self.n, 3))
-        lib().orc_get_forces(self._h, _dptr(out))
+        self._L.orc_get_forces(self._h, _dptr(out))
         return out
 
     def lattice_energy(self):
         k, m = C.c_double(), C.c_double()
-        lib().orc_lattice_energy(self._h, C.byref(k), C.byref(m))
+        self._L.orc_lattice_energy(self._h, C.byref(k), C.byref(m))
         return k.value, m.value
 
     def total_energy(self):
@@ -413,8 +425,8 @@ class Oracle:
 
     @property
     def colour_violations(self):
-        return lib().orc_colour_violations(self._h)
+        return self._L.orc_colour_violations(self._h)
 
     @property
     def ion_energy_to_electrons(self):
-        return lib().orc_ion_energy_to_electrons(self._h)
+        return self._L.orc_ion_energy_to_electrons(self._h)

@@ -25,5 +25,17 @@ def build(force: bool = False) -> str:
     return LIB
 
 
+def build_variant(defines, outdir) -> str:
+    """Build a deliberately altered copy of the oracle (each entry of
+    `defines` one ORC_PLANT_* switch) into outdir, for the tests that check
+    a pin fails on a planted mistake.  Never used outside the test suite."""
+    os.makedirs(outdir, exist_ok=True)
+    out = os.path.join(outdir, "libtts_oracle_%s.so" % "_".join(d.lower() for d in defines))
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-Wall", *("-D" + d for d in defines), "-o", out, SRC, "-lm"]
+    subprocess.check_call(cmd)
+    return out
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv))

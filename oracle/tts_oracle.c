@@ -684,11 +684,27 @@ int orc_set_ttm(orc_sys *S, const orc_ttm *t, char *err, int errlen)
                 int c = (cz * t->ncy + cy) * t->ncx + cx;
                 double x = (cx + 0.5) * S->box[0] / t->ncx, y = (cy + 0.5) * S->box[1] / t->ncy;
                 double z = (cz + 0.5) * S->box[2] / t->ncz;
+                /* laser spot (Sec. II.B source): a Gaussian of width sigma_xy
+                 * centred on the box in x-y, or an exponential absorption
+                 * profile exp(-z / depth) from the z = 0 face, at cell centres.
+                 * The ORC_PLANT_* switches build deliberately wrong variants
+                 * for the tests that show the source pins catch such errors;
+                 * the normal build defines none of them. */
+                double xc = 0.5 * S->box[0], yc = 0.5 * S->box[1], w2 = 2.0 * sq(t->sigma_xy), zs = -1.0;
+#ifdef ORC_PLANT_SPOT_NO_HALF
+                w2 = sq(t->sigma_xy);
+#endif
+#ifdef ORC_PLANT_SPOT_OFF_CENTRE
+                xc += 0.5 * S->box[0] / t->ncx;
+#endif
+#ifdef ORC_PLANT_DEPTH_SIGN
+                zs = 1.0;
+#endif
                 double f = 1.0;
                 if (t->spatial == 1)
-                    f = exp(-(sq(x - 0.5 * S->box[0]) + sq(y - 0.5 * S->box[1])) / (2.0 * sq(t->sigma_xy)));
+                    f = exp(-(sq(x - xc) + sq(y - yc)) / w2);
                 else if (t->spatial == 2)
-                    f = exp(-z / t->depth_z);
+                    f = exp(zs * z / t->depth_z);
                 S->src_shape[c] = f;
             }
     /* sub-steps: smallest m with dt/m <= 0.4 C_e(T0) dx_min^2 / (kappa_e d) */
