@@ -136,6 +136,11 @@ TTS_API int tts_ttm_advance_noalloc(const tts_ttm_desc *t, const double box_ang[
     for (int k = 0; k < 3; ++k) {
         if (t->cells[k] < 1) return noalloc_fail(TTS_ERR_ARG, "TTM cell counts must be >= 1");
         if (!(box_ang[k] > 0.0)) return noalloc_fail(TTS_ERR_ARG, "box edges must be positive");
+        // checked before multiplying, so that the product cannot overflow
+        if (t->cells[k] > kNoAllocMaxCells / nc)
+            return noalloc_fail(TTS_ERR_ARG, "grid has more than " + std::to_string(kNoAllocMaxCells) +
+                                                 " cells; this entry point handles at most " +
+                                                 std::to_string(kNoAllocMaxCells));
         nc *= t->cells[k];
     }
     if (nc > kNoAllocMaxCells)
@@ -145,6 +150,10 @@ TTS_API int tts_ttm_advance_noalloc(const tts_ttm_desc *t, const double box_ang[
         return noalloc_fail(TTS_ERR_ARG, "TTM coefficients out of range");
     if (t->source < 0 || t->source > 2 || t->spatial < 0 || t->spatial > 2) return noalloc_fail(TTS_ERR_ARG, "bad TTM mode");
     if (t->source != TTS_SOURCE_NONE && !(fwhm > 0.0)) return noalloc_fail(TTS_ERR_ARG, "pulse FWHM must be positive");
+    if (t->spatial == TTS_SPATIAL_XY_GAUSS && !(t->sigma_xy > 0.0))
+        return noalloc_fail(TTS_ERR_ARG, "the Gaussian spot needs sigma_xy > 0");
+    if (t->spatial == TTS_SPATIAL_Z_EXP && !(t->depth_z > 0.0))
+        return noalloc_fail(TTS_ERR_ARG, "the exponential profile needs depth_z > 0");
     double *scratch = nullptr;
     int rc = scratch_for_current_device(&scratch);
     if (rc) return rc;

@@ -2,6 +2,7 @@
 // memory, the captured per-step CUDA graph, TTM set-up and calibration,
 // observables, checkpoints.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -702,6 +703,18 @@ int tts_set_ttm_grid(tts_system *s, const tts_ttm_desc *t)
     const bool profile = t->source == TTS_SOURCE_STEP_PROFILE;
     if (profile && s->lat) return fail(TTS_ERR_UNSUPPORTED, "the step profile is for rigid lattices");
     if (profile && !(t->t0 >= 0.0)) return fail(TTS_ERR_ARG, "step profile: t0 (first stage) must be >= 0");
+    if (t->spatial == TTS_SPATIAL_XY_GAUSS && !(t->sigma_xy > 0.0))
+        return fail(TTS_ERR_ARG, "the Gaussian spot needs sigma_xy > 0");
+    if (t->spatial == TTS_SPATIAL_Z_EXP && !(t->depth_z > 0.0))
+        return fail(TTS_ERR_ARG, "the exponential profile needs depth_z > 0");
+    {
+        // cells over all instances must fit the int indices of the grid kernels
+        int64_t cells = s->n_inst;
+        for (int k = 0; k < 3; ++k) {
+            if (t->cells[k] > INT_MAX / cells) return fail(TTS_ERR_ARG, "TTM grid too large");
+            cells *= t->cells[k];
+        }
+    }
     TTS_CUDA(cudaStreamSynchronize(s->stream), "set ttm");
     const int nc = t->cells[0] * t->cells[1] * t->cells[2];
     const int total = nc * s->n_inst;

@@ -78,3 +78,20 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(P, "_LIB", None)
     with pytest.raises(ImportError):
         P.load()
+
+
+@pytest.mark.parametrize("change,msg", [
+    (dict(spatial="xy_gauss", sigma_xy=0.0), "sigma_xy > 0"),
+    (dict(spatial="z_exp", depth_z=0.0), "depth_z > 0"),
+    (dict(cells=[2 ** 21, 2 ** 21, 2 ** 22]), "at most 65536"),
+    (dict(cells=[65537, 1, 1]), "at most 65536"),
+    (dict(cells=[41, 40, 40]), "at most 65536"),
+    (dict(cells=[0, 4, 4]), ">= 1"),
+])
+def test_noalloc_arguments_are_checked_on_the_host(lib, change, msg):
+    # rejected before any device work: the buffers are never touched
+    t = dict(W.ttm_xy_spot(8), source="power", P0=1e20)
+    t.update(change)
+    with pytest.raises(P.TTSError) as ei:
+        P.ttm_advance_noalloc(t, [100.0, 100.0, 100.0], 1e-16, 0, 0x1000, 0x2000)
+    assert ei.value.code == -1 and msg in str(ei.value)
