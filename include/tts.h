@@ -140,7 +140,7 @@ typedef struct {
 #define TTS_SOURCE_PEAK 1          /* calibrate P0 so that max T_e over cells and steps = peak_Te */
 #define TTS_SOURCE_POWER 2         /* use P0 as given */
 #define TTS_SOURCE_STEP_PROFILE 3  /* prescribed electron temperature, the three-stage step profile
-                                      of the paper's GdFeCo runs (Sec. II.E): T_e = peak_Te for
+                                      of the paper's GdFeCo runs (Sec. II.D): T_e = peak_Te for
                                       t < t0, peak_Te / 2 for t0 <= t < t0 + fwhm, T0 after; T_l = T0.
                                       No grid equation (gamma_e, C_l, G, kappa_e unused); peak_Te
                                       and fwhm (the second stage) take the per-instance overrides;
@@ -232,17 +232,34 @@ TTS_API int tts_destroy(tts_system *sys);
 TTS_API int tts_set_ttm_grid(tts_system *sys, const tts_ttm_desc *ttm);
 
 /* Advance every instance by nsteps time steps (asynchronous).  One step:
- * noise amplitudes from T_e(t_n); the symmetric colour sweep; the TTM grid
- * from t_n to t_n+1; observables at t_n+1 when the step count reaches a
- * multiple of sample_every.  Errors: TTS_ERR_ARG (nsteps < 0), TTS_ERR_CUDA. */
+ * noise amplitudes from T_e(t_n), the variance 2 alpha k_B T_e / (gamma mu_i h)
+ * of the thermal field of the bath coupled to the electron temperature
+ * (Eq. 2, Sec. II.B) with the 1/mu_i torque and 1/sqrt(mu_i) noise scaling of
+ * Sec. II.C; the stochastic LLG equation (Eq. 1, Sec. II.A) integrated by the
+ * symplectic Suzuki-Trotter splitting of Sec. II.A, done as a symmetric sweep
+ * over colour classes (each sub-step the exact flow of Eq. 1 under the field
+ * held fixed for it); the TTM grid from t_n to t_n+1 (Sec. II.B); observables
+ * at t_n+1 when the step count reaches a multiple of sample_every.  Work is
+ * queued on the system's stream and nothing is read back.
+ * Errors: TTS_ERR_ARG (nsteps < 0), TTS_ERR_CUDA (a launch failed). */
 TTS_API int tts_step(tts_system *sys, int64_t nsteps);
 
-/* Wait for queued work and check the device health word.  Errors:
- * TTS_ERR_HEALTH (non-finite spin), TTS_ERR_DEVICE_TIMEOUT, TTS_ERR_CUDA. */
+/* Wait for queued work and check the device health word.  The paper has no
+ * counterpart (its runs are CPU processes): this is the failure check of the
+ * device path.  A flagged fault stays flagged for the life of the system
+ * (rebuild it, or restore a checkpoint into a new one).  Errors:
+ * TTS_ERR_HEALTH (a non-finite spin; with a moving lattice also an atom
+ * beyond half its skin, two exchange-coupled atoms of one colour, or a full
+ * neighbour table), TTS_ERR_DEVICE_TIMEOUT (a bounded device-side wait ran
+ * out; the kernel that waited returned early), TTS_ERR_CUDA. */
 TTS_API int tts_sync(tts_system *sys);
 
 /* Copy up to max_samples observable records of one instance, oldest first,
- * TTS_NOBS doubles each:
+ * TTS_NOBS doubles each.  These are the quantities the paper follows: the
+ * sublattice magnetisations whose z components define switching (Sec. II.G),
+ * the energies of the Hamiltonian of Sec. II.A, and the per-sublattice spin
+ * temperature of the "compute spin" estimator (Sec. III.A), all reduced in
+ * FP64 in a fixed order:
  *  [0] t  [1..3] mean s of species 0  [4..6] mean s of species 1
  *  [7..9] sum(mu_i s_i)/sum(mu_i)  [10] -sum_{i<j} J_ij s_i.s_j
  *  [11] -sum K (s.n)^2  [12] -sum mu_i B.s_i  [13..14] spin temperature per

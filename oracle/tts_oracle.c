@@ -572,7 +572,7 @@ static int cidx(const orc_sys *S, int cx, int cy, int cz)
 /* use_G = 0 drops the G (T_e - T_l) exchange: with a moving lattice the ions
  * exchange energy with the electrons through their own friction and noise. */
 /* The three-stage electron-temperature profile of the paper's GdFeCo runs
- * (Sec. II.E): peak, half the peak, then the base temperature. */
+ * (Sec. II.D): peak, half the peak, then the base temperature. */
 static double profile_Te(const orc_ttm *t, double tt)
 {
     if (tt < t->t0) return t->peak_Te;

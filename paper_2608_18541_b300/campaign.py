@@ -1,4 +1,4 @@
-"""Switching campaign of the paper's GdFeCo protocol (Sec. II.E, II.G) on one
+"""Switching campaign of the paper's GdFeCo protocol (Sec. II.D, II.G) on one
 GPU: every (peak T_e, cooling multiplier d, realisation) is an instance of one
 batched system; prints the switching probability per (peak, d) with its
 Wilson 95 % interval, and the throughput.

@@ -185,7 +185,7 @@ def curie_scan(temps, n=6, reps=2, alpha=0.5, dt=1.0 * FS, seed=42):
     return s
 
 
-# GdFeCo on fcc (Sec. II.E, Table I): literature amplitudes J1 per species
+# GdFeCo on fcc (Sec. II.D, Table I; shape re-derived as in Sec. II.E): literature amplitudes J1 per species
 # pair, the radial shape re-derived for the fcc nearest-neighbour distance
 # a / sqrt(2) (J2 = 0.4050, J3 = 3.1677 A), cutoff 3.4 A between the first two
 # shells, K = 5.0384e-5 eV, alpha = 0.01, no field.

@@ -1,5 +1,5 @@
 """The paper's GdFeCo protocol on the GPU: fcc lattice, Bethe-Slater exchange
-re-derived for fcc, the three-stage step profile of T_e (Sec. II.E) with a
+re-derived for fcc, the three-stage step profile of T_e (Sec. II.D) with a
 per-instance peak and cooling stage, against the oracle state by state; and
 the switching statistics of a small campaign (Sec. II.G)."""
 import numpy as np

@@ -1,5 +1,5 @@
 """Host-side switching statistics (paper Sec. II.G) and the step-profile
-bath of the oracle (Sec. II.E)."""
+bath of the oracle (Sec. II.D)."""
 import numpy as np
 import pytest
 
