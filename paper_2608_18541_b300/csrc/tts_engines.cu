@@ -571,10 +571,14 @@ __global__ void __launch_bounds__(256, 3) checker_pair_tiled_kernel(PairArgs a, 
 }
 
 // Observables of the pair layout: the same per-species partial sums, block
-// by block, as the general observable kernel.  Per site, in FP32 and tesla:
-// the unit-free terms 1, s, s.h, (s.n)^2, B.s, |s x B_tot|^2, s.B_tot (h the
-// exchange field, B_tot = h + kappa (s.n) n + B), summed over the thread's 8
-// sites; then scaled by mu and K of the species and summed in FP64.
+// by block, as the general observable kernel.  Per site, in FP32 and tesla
+// (the spins are FP32): the unit-free terms s, s.h, (s.n)^2, B.s,
+// |s x B_tot|^2, s.B_tot (h the exchange field, B_tot = h + kappa (s.n) n + B).
+// Every sum over sites is FP64: each site's terms are converted exactly to
+// double and added to FP64 accumulators per species (species-1 sums by a
+// fused multiply-add with the 0/1 species flag, species 0 as the difference
+// from the all-site sum); the block then reduces the threads' accumulators in
+// a fixed order and scales them by mu and K of the species.
 struct PairObsArgs {
     const int *obs_block_inst;
     const DevInstance *inst;
@@ -584,7 +588,46 @@ struct PairObsArgs {
     double mu[TTS_MAX_SPECIES], K[TTS_MAX_SPECIES];
 };
 
-constexpr int kObsTerms = 9;
+// Factor of observable field f (12 per species): 1 for the count and the sums
+// of s; -mu/2 (exchange), -K, -mu (Zeeman), mu^2 (|s x H|^2), mu (s.H).
+__device__ __forceinline__ double obs_scale(const PairObsArgs &o, int f)
+{
+    const int sp = f >= 12 ? 1 : 0, r = f - 12 * sp;
+    const double mu = sp ? o.mu[1] : o.mu[0], K = sp ? o.K[1] : o.K[0];
+    switch (r) {
+    case 7: return -0.5 * mu;
+    case 8: return -K;
+    case 9: return -mu;
+    case 10: return mu * mu;
+    case 11: return mu;
+    default: return 1.0;
+    }
+}
+
+constexpr int kObsTerms = 8;
+
+// Sum NF doubles over the kObsBlock threads: shared memory, then warp w sums
+// the fields f = w, w + 4, ... (each lane four threads' values, then a
+// five-level shuffle tree): a fixed order, about a fifth of the FP64 adds of
+// a shuffle tree over every field in every lane.
+// The sum of field f is multiplied by scale(f) and stored at out[f].
+template <int NF, typename Scale>
+__device__ __forceinline__ void block_sum_fields(const double (&v)[NF], Scale scale, double *out)
+{
+    static_assert(kObsBlock == 128, "four warps of 32");
+    __shared__ double sh[NF][kObsBlock];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) sh[f][threadIdx.x] = v[f];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int f = warp; f < NF; f += kObsBlock / 32) {
+        double x = (sh[f][lane] + sh[f][lane + 32]) + (sh[f][lane + 64] + sh[f][lane + 96]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) out[f] = x * scale(f);
+    }
+    __syncthreads();
+}
 
 __global__ void __launch_bounds__(kObsBlock) checker_pair_obs_kernel(PairArgs a, PairObsArgs o, int mode)
 {
@@ -595,9 +638,10 @@ __global__ void __launch_bounds__(kObsBlock) checker_pair_obs_kernel(PairArgs a,
     for (int blk = blockIdx.x; blk < o.obs_blocks; blk += gridDim.x) {
         const int inst = o.obs_block_inst[blk];
         const uint32_t local = static_cast<uint32_t>(blk - o.inst[inst].obs_block_begin);
-        f2 c0[kObsTerms], c1[kObsTerms];
+        double all[kObsTerms], one[kObsTerms];
 #pragma unroll
-        for (int t = 0; t < kObsTerms; ++t) c0[t] = c1[t] = f2{0};
+        for (int t = 0; t < kObsTerms; ++t) all[t] = one[t] = 0.0;
+        int n_all = 0, n_one = 0;
         const ulonglong2 *base = a.S + int64_t(inst) * a.n_inst_sites;
         for (int j = 0; j < kObsSpan / 2 / kObsBlock; ++j) {
             const uint32_t P = local * (kObsSpan / 2) + threadIdx.x + uint32_t(j) * kObsBlock;
@@ -622,8 +666,7 @@ __global__ void __launch_bounds__(kObsBlock) checker_pair_obs_kernel(PairArgs a,
             const f2 ka = kap * sn;
             const f2 Bx = fma2(ka, k.nx, hX + k.Bx), By = fma2(ka, k.ny, hY + k.By), Bz = fma2(ka, k.nz, hZ + k.Bz);
             const f2 cx = sy * Bz - sz * By, cy = sz * Bx - sx * Bz, cz = sx * By - sy * Bx;
-            const f2 term[kObsTerms] = {k.one,
-                                        sx,
+            const f2 term[kObsTerms] = {sx,
                                         sy,
                                         sz,
                                         fma2(sz, hZ, fma2(sy, hY, sx * hX)),
@@ -631,38 +674,37 @@ __global__ void __launch_bounds__(kObsBlock) checker_pair_obs_kernel(PairArgs a,
                                         fma2(sz, k.Bz, fma2(sy, k.By, sx * k.Bx)),
                                         fma2(cz, cz, fma2(cy, cy, cx * cx)),
                                         fma2(sz, Bz, fma2(sy, By, sx * Bx))};
-            const f2 m0 = k.one - w;
+            float wA, wB;
+            f2_split(w, wA, wB);
+            const double dwA = wA, dwB = wB;
+            n_all += 2;
+            n_one += (wA != 0.0f) + (wB != 0.0f);
 #pragma unroll
             for (int t = 0; t < kObsTerms; ++t) {
-                c0[t] = fma2(m0, term[t], c0[t]);
-                c1[t] = fma2(w, term[t], c1[t]);
+                float vA, vB;
+                f2_split(term[t], vA, vB);
+                const double dA = vA, dB = vB;
+                all[t] += dA;
+                all[t] += dB;
+                one[t] = fma(dwA, dA, one[t]);
+                one[t] = fma(dwB, dB, one[t]);
             }
         }
         double acc[kObsFields];
 #pragma unroll
         for (int f = 0; f < kObsFields; ++f) acc[f] = 0.0;
+        acc[0] = double(n_all - n_one);
+        acc[12] = double(n_one);
 #pragma unroll
-        for (int sp = 0; sp < 2; ++sp) {
-            double v[kObsTerms];
-#pragma unroll
-            for (int t = 0; t < kObsTerms; ++t) {
-                float l, h;
-                f2_split(sp ? c1[t] : c0[t], l, h);
-                v[t] = double(l) + double(h);
-            }
-            const double mu = o.mu[sp], K = o.K[sp];
-            double *q = acc + 12 * sp;
-            q[0] = v[0];
-            q[1] = v[1];
-            q[2] = v[2];
-            q[3] = v[3];
-            q[7] = -0.5 * mu * v[4];
-            q[8] = -K * v[5];
-            q[9] = -mu * v[6];
-            q[10] = mu * mu * v[7];
-            q[11] = mu * v[8];
+        for (int t = 0; t < kObsTerms; ++t) {
+            // species 0: all sites minus species 1, term by term
+            const double v0 = all[t] - one[t], v1 = one[t];
+            const int f = t < 3 ? 1 + t : 4 + t;       // s -> 1..3; the five others -> 7..11
+            acc[f] = v0;
+            acc[12 + f] = v1;
         }
-        block_sum_store<kObsFields>(acc, o.obs_partial + int64_t(blk) * kObsFields);
+        block_sum_fields<kObsFields>(acc, [&](int f) { return obs_scale(o, f); },
+                                     o.obs_partial + int64_t(blk) * kObsFields);
     }
 }
 

@@ -1,6 +1,7 @@
-"""The reference arm of bench.py (the FP64 oracle timed on the host cores):
-one JSON line with the benchmark's metric and config on rank 0, nothing on
-the other ranks.  Runs on the 32^3 GdFeCo workload so it stays short."""
+"""The reference arm of bench.py (the FP64 oracle timed on the host cores,
+one single-threaded process per realisation, all at once): one JSON line with
+the benchmark's metric and config on rank 0, nothing on the other ranks.
+Runs on the 32^3 GdFeCo workload with two processes so it stays short."""
 import json
 import os
 import subprocess
@@ -13,7 +14,7 @@ def _run(extra_env=None, *args):
     env = dict(os.environ)
     env.update(extra_env or {})
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "gdfeco_32",
-           "--steps", "2", "--warmup", "1", *args]
+           "--steps", "2", "--warmup", "1", "--cpu-procs", "2", *args]
     return subprocess.run(cmd, capture_output=True, text=True, timeout=600, env=env, cwd=ROOT)
 
 
@@ -30,7 +31,10 @@ def test_reference_arm_line():
     assert d["value"] > 0
     assert d["config"]["sample_every"] == 100          # default: once per 100-step chunk
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
-    assert d["cpu_baseline"]["cores"] == 1
+    c = d["cpu_baseline"]
+    assert c["cores"] == 2 and c["nproc"] == os.cpu_count()
+    assert c["aggregate"] == d["value"] and 0 < c["per_core"] <= c["aggregate"]
+    assert "2 concurrent" in c["sample"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
