@@ -176,6 +176,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) checker_pass_kern
 // ---------------------------------------------------------------------------
 struct PairArgs {
     ulonglong2 *S;               // all instances: [inst][colour][lo | hi plane][pair]
+    ulonglong2 *S1;              // second state buffer of the fused sweep (= S without it)
+    const int *cur;              // 1: the current state is in S1, else in S
     const int *cell;             // general slot -> TTM cell
     const float *sigma;          // [cell][species][h]
     const int64_t *step;
@@ -205,6 +207,11 @@ struct PairArgs {
 struct Pair4 {
     f2 x, y, z, w;
 };
+
+// The buffer holding the current state: the fused sweep reads one buffer and
+// writes the other, then flips *cur; every other kernel of the pair layout
+// works on the current buffer in place.
+__device__ __forceinline__ ulonglong2 *pair_state(const PairArgs &a) { return *a.cur ? a.S1 : a.S; }
 
 __device__ __forceinline__ Pair4 load_pair(const ulonglong2 *lo, const ulonglong2 *hi, uint32_t q)
 {
@@ -365,7 +372,7 @@ __device__ __forceinline__ void pair_block(const PairArgs &a, int colour, int hs
     if (a.pf_planes > 0 && threadIdx.x == 0 && threadIdx.y == 0 && z + a.pf_planes < Lz) {
         const uint32_t zf = z + a.pf_planes, y0 = yb * blockDim.y, kx0 = (bx - yb * a.nkx) * blockDim.x;
         const uint32_t rows = min(blockDim.y, Ly2 - y0), cols = min(blockDim.x, hx - kx0);
-        const ulonglong2 *ib = a.S + int64_t(inst) * a.n_inst_sites;
+        const ulonglong2 *ib = pair_state(a) + int64_t(inst) * a.n_inst_sites;
         for (uint32_t r = 0; r < rows; ++r) {
             const uint32_t q = (zf * Ly2 + y0 + r) * hx + kx0;
             bulk_prefetch_l2(ib + q, cols * 16u);                           // colour 0, lo plane
@@ -378,7 +385,7 @@ __device__ __forceinline__ void pair_block(const PairArgs &a, int colour, int hs
     const PairSite p = make_site(a, inst, z, y2, kx, colour);
     f2 g1{0}, g2{0}, g3{0};
     if (a.noise) site_noise(a, p, static_cast<uint32_t>(*a.step), pass, g1, g2, g3);
-    ulonglong2 *base = a.S + int64_t(inst) * a.n_inst_sites;
+    ulonglong2 *base = pair_state(a) + int64_t(inst) * a.n_inst_sites;
     const ulonglong2 *Olo = base + (colour ? 0 : a.nhalf);
     const ulonglong2 *Ohi = Olo + a.npair;
     ulonglong2 *Wlo = base + (colour ? a.nhalf : 0);
@@ -476,7 +483,7 @@ __global__ void __launch_bounds__(256, 3) checker_pair_tiled_kernel(PairArgs a, 
         const uint32_t zb = static_cast<uint32_t>(min(uint64_t(Lz), za + (u_end - u)));
         const int inst = static_cast<int>(col / t.nyb);
         const uint32_t y0 = (col - uint32_t(inst) * t.nyb) * by;
-        const ulonglong2 *gbase = a.S + int64_t(inst) * a.n_inst_sites;
+        const ulonglong2 *gbase = pair_state(a) + int64_t(inst) * a.n_inst_sites;
         const ulonglong2 *go = gbase + (other ? a.nhalf : 0);
         ulonglong2 *gw = const_cast<ulonglong2 *>(gbase) + (colour ? a.nhalf : 0);
         // thread 0: copy tile rows y0 - 1 .. y0 + by of other-colour plane zz
@@ -570,6 +577,396 @@ __global__ void __launch_bounds__(256, 3) checker_pair_tiled_kernel(PairArgs a, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fused symmetric sweep (FP32 site pairs, two colours): the three colour
+// passes of a time step -- colour 0 for dt/2, colour 1 for dt, colour 0 for
+// dt/2 -- in one launch, as a wavefront along z (temporal blocking), so that
+// the state crosses HBM about once a step instead of three times.
+//
+// A cluster of C CTAs owns one z segment [z0, z1) of one instance; CTA r of
+// the cluster owns pair rows [r R, r R + R) of every plane (C R = Ly/2), one
+// pair column a thread, a third of the threads per pass.  At wavefront step
+// t, with p0 = z0 - 2 + t, the CTA runs
+//   pass 0 (colour 0, dt/2) on plane p0 + 2    (ahead, see below),
+//   pass 1 (colour 1, dt)   on plane p0 - 2,
+//   pass 2 (colour 0, dt/2) on plane p0 - 4.
+// A pass on plane P needs the previous pass on P - 1, P and P + 1; with a lag
+// of two planes those finished at earlier steps, so one cluster barrier a
+// step orders everything.  Pass 0 reads only the state at the start of the
+// step, so the pass-0 threads run the next step's plane while the other
+// threads finish the current one.  The CTA's rows of the planes in flight
+// live in shared memory: rings of 9 colour-1 and 8 colour-0 plane tiles,
+// filled by bulk copies two steps ahead (the colour-1 halo rows y0 - 1 and
+// y0 + R that pass 0 needs come with them, from global memory).  Passes 1 and
+// 2 read the halo rows -- results of the neighbouring CTAs' earlier passes --
+// from those CTAs' shared memory.  Pass 0 runs on planes z0 - 2 .. z1 + 1 and
+// pass 1 on z0 - 1 .. z1, so that pass 2 has all it needs on z0 .. z1 - 1:
+// neighbouring segments recompute two planes each side, which needs the
+// input state unchanged while they run, so the kernel reads one state buffer
+// and writes the other (and the last CTA to finish flips *cur).  Every site
+// gets the same inputs, noise and arithmetic as in the three separate passes,
+// so the spins are bitwise those of checker_pair_kernel.
+// ---------------------------------------------------------------------------
+struct SweepShape {
+    uint32_t R = 0, C = 0;       // pair rows per CTA, CTAs per cluster (C R = Ly/2); C == 0: not offered
+    uint32_t nseg = 1;           // z segments per instance
+    uint32_t threads = 0;        // 3 R hx
+    size_t smem = 0;
+};
+
+struct SweepArgs {
+    uint32_t R, nseg;
+    unsigned *done;              // CTAs finished; the last one flips *cur and clears this
+    uint32_t ctas;
+    int *cur;                    // writable view of PairArgs::cur
+};
+
+constexpr int kSwD1 = 9, kSwD0 = 8, kSwDH = 3;
+
+inline size_t sweep_smem_bytes(uint32_t RH, uint32_t hx)
+{
+    return size_t(2u * (kSwD1 + kSwD0) * RH + 2u * kSwDH * 2u * hx) * 16u + 3 * sizeof(uint64_t);
+}
+
+__device__ __forceinline__ void cluster_arrive()
+{
+    asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait()
+{
+    asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// 16-byte loads from this CTA's shared memory and from a peer CTA's
+// (distributed shared memory), by 32-bit shared-window addresses
+__device__ __forceinline__ ulonglong2 lds16(uint32_t addr)
+{
+    ulonglong2 v;
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ ulonglong2 ldsc16(uint32_t addr)
+{
+    ulonglong2 v;
+    asm volatile("ld.shared::cluster.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ void sts16(uint32_t addr, ulonglong2 v)
+{
+    asm volatile("st.shared.v2.u64 [%0], {%1, %2};" ::"r"(addr), "l"(v.x), "l"(v.y) : "memory");
+}
+__device__ __forceinline__ uint32_t peer_addr(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+template <bool AXZ>
+__global__ void __launch_bounds__(768, 1) checker_sweep_kernel(PairArgs a, SweepArgs w)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t hx = a.hx, Ly2 = a.Ly2, Lz = a.Lz, R = w.R, RH = R * hx;
+    ulonglong2 *c1 = reinterpret_cast<ulonglong2 *>(smem);      // [kSwD1][lo RH | hi RH]
+    ulonglong2 *c0 = c1 + 2u * kSwD1 * RH;                        // [kSwD0][lo RH | hi RH]
+    ulonglong2 *hl = c0 + 2u * kSwD0 * RH;                        // [kSwDH][lo: y0-1, y0+R | hi: y0-1, y0+R]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(hl + 2u * kSwDH * 2u * hx);
+    __shared__ int s_late;
+
+    const uint32_t C = gridDim.x, rank = blockIdx.x, seg = blockIdx.y, inst = blockIdx.z;
+    const uint32_t y0 = rank * R;
+    const int z0 = static_cast<int>(uint64_t(seg) * Lz / w.nseg), z1 = static_cast<int>(uint64_t(seg + 1) * Lz / w.nseg);
+    const int Z = z1 - z0, last_batch = Z + 3;
+    const int cur = *a.cur;
+    const ulonglong2 *in = (cur ? a.S1 : a.S) + int64_t(inst) * a.n_inst_sites;
+    ulonglong2 *out = (cur ? a.S : a.S1) + int64_t(inst) * a.n_inst_sites;
+    const ulonglong2 *in0 = in, *in1 = in + a.nhalf;             // colour 0 / 1, lo plane (hi at + npair)
+
+    auto zwrap = [&](int p) {                                    // p in [-Lz, 2 Lz)
+        return static_cast<uint32_t>(p < 0 ? p + static_cast<int>(Lz) : (p >= static_cast<int>(Lz) ? p - static_cast<int>(Lz) : p));
+    };
+    auto tile1 = [&](int p) { return c1 + 2u * RH * (static_cast<uint32_t>(p - (z0 - 3)) % kSwD1); };
+    auto tile0 = [&](int p) { return c0 + 2u * RH * (static_cast<uint32_t>(p - (z0 - 3)) % kSwD0); };
+
+    // batch u: the CTA's colour-1 rows of plane p0(u) + 1 and colour-0 rows of
+    // p0(u), and the colour-1 halo rows at p0(u); batch 0 also brings the
+    // colour-1 rows of p0(0) - 1 and p0(0)
+    auto issue = [&](int u) {
+        const int p0 = z0 - 2 + u;
+        uint64_t *b = bar + (u % 3);
+        const uint32_t rb = RH * 16u, hb = hx * 16u;
+        mbar_arrive_expect_tx(b, (u == 0 ? 8u : 4u) * rb + 4u * hb);
+        auto rows = [&](const ulonglong2 *src, int p, ulonglong2 *dst) {
+            const uint32_t q = (zwrap(p) * Ly2 + y0) * hx;
+            bulk_copy_g2s(dst, src + q, rb, b);
+            bulk_copy_g2s(dst + RH, src + a.npair + q, rb, b);
+        };
+        if (u == 0) {
+            rows(in1, p0 - 1, tile1(p0 - 1));
+            rows(in1, p0, tile1(p0));
+        }
+        rows(in1, p0 + 1, tile1(p0 + 1));
+        rows(in0, p0, tile0(p0));
+        ulonglong2 *h = hl + (u % kSwDH) * 4u * hx;
+        const uint32_t zz = zwrap(p0);
+        const uint32_t qm = (zz * Ly2 + (y0 + Ly2 - 1) % Ly2) * hx, qp = (zz * Ly2 + (y0 + R) % Ly2) * hx;
+        bulk_copy_g2s(h, in1 + qm, hb, b);
+        bulk_copy_g2s(h + hx, in1 + qp, hb, b);
+        bulk_copy_g2s(h + 2u * hx, in1 + a.npair + qm, hb, b);
+        bulk_copy_g2s(h + 3u * hx, in1 + a.npair + qp, hb, b);
+    };
+
+    // ---- this thread: pass g on pair column jcol (row r, colour site kx) ----
+    const uint32_t tid = threadIdx.x;
+    const uint32_t g = tid / RH, jcol = tid - g * RH;
+    const uint32_t r = jcol / hx, kx = jcol - r * hx, y2 = y0 + r;
+    const int colour = g == 1 ? 1 : 0;
+    const uint32_t kxp = kx + 1 == hx ? 0 : kx + 1, kxm = kx == 0 ? hx - 1 : kx - 1;
+    const uint32_t step = static_cast<uint32_t>(*a.step);
+    const uint32_t ig = a.inst_base + inst;
+    const uint32_t peer_up = rank + 1 == C ? 0 : rank + 1, peer_dn = rank == 0 ? C - 1 : rank - 1;
+    // shared-window byte addresses: own ring (this pass's colour), other ring, halo slots
+    const uint32_t tileB = 2u * RH * 16u, hiB = RH * 16u;
+    const uint32_t own_base = smem_u32(colour ? c1 : c0), oth_base = smem_u32(colour ? c0 : c1);
+    const uint32_t Down = colour ? kSwD1 : kSwD0, Doth = colour ? kSwD0 : kSwD1;
+    const uint32_t halo_base = smem_u32(hl);
+    const uint32_t colB = jcol * 16u;
+    // invariants of the site pair's noise counter and TTM cell
+    const uint32_t atom_row = y2 * a.Lx + 2 * kx, plane_atoms = a.Ly * a.Lx;
+    const uint32_t cell_inst = static_cast<uint32_t>(a.cell0 + static_cast<int>(inst) * a.cstride);
+    auto cc = [](uint32_t v, uint32_t n, const FastDiv &d, int sh) { return sh >= 0 ? v >> sh : fast_div(v * n, d); };
+    const uint32_t cyA = cc(y2, a.ncy, a.dLy, a.shy), cyB = cc(y2 + Ly2, a.ncy, a.dLy, a.shy);
+    const uint32_t cx0 = cc(2 * kx, a.ncx, a.dLx, a.shx), cx1 = cc(2 * kx + 1, a.ncx, a.dLx, a.shx);
+    const int hsel = colour;
+    const uint32_t par_flip = Ly2 & 1u;
+
+    // prepared for the next pass of this thread (independent of any spin):
+    // its plane, noise directions and the noise amplitudes of both species
+    struct Prep {
+        int P;
+        uint32_t zP, parA;
+        uint32_t so, sm, s0, sp;     // ring slots: own tile of P; other tiles of P - 1, P, P + 1
+        f2 g1, g2, g3;
+        float sA[2], sB[2];
+    };
+    // ring-slot byte offsets advance one tile a step (a pass moves one plane)
+    const uint32_t own_wrap = Down * tileB, oth_wrap = Doth * tileB;
+    auto adv = [](uint32_t v, uint32_t step_b, uint32_t wrap) { v += step_b; return v == wrap ? 0u : v; };
+    auto prepare = [&](int t, Prep &q, bool fresh) {
+        q.P = z0 - 2 + t - 2 * static_cast<int>(g);
+        q.zP = zwrap(q.P);
+        if (fresh) {
+            const uint32_t rel = static_cast<uint32_t>(q.P - (z0 - 3));
+            q.so = (rel % Down) * tileB;
+            q.sm = ((rel - 1) % Doth) * tileB;
+            q.s0 = (rel % Doth) * tileB;
+            q.sp = ((rel + 1) % Doth) * tileB;
+        } else {
+            q.so = adv(q.so, tileB, own_wrap);
+            q.sm = adv(q.sm, tileB, oth_wrap);
+            q.s0 = adv(q.s0, tileB, oth_wrap);
+            q.sp = adv(q.sp, tileB, oth_wrap);
+        }
+        q.parA = (y2 + q.zP + uint32_t(colour)) & 1u;
+        const uint32_t parB = q.parA ^ par_flip;
+        q.g1 = q.g2 = q.g3 = f2{0};
+        q.sA[0] = q.sA[1] = q.sB[0] = q.sB[1] = 0.0f;
+        if (a.noise) {
+            const uint32_t atomA = q.zP * plane_atoms + atom_row + q.parA;
+            const uint32_t atomB = atomA + Ly2 * a.Lx + parB - q.parA;
+            pair_noise(u32x4{atomA, step, g, ig}, u32x4{atomB, step, g, ig}, a.rk, a.k, q.g1, q.g2, q.g3);
+            int cA, cB;
+            if (a.cell_formula) {
+                const uint32_t cz = cc(q.zP, a.ncz, a.dLz, a.shz);
+                const uint32_t base = cell_inst + cz * a.ncy * a.ncx;
+                cA = static_cast<int>(base + cyA * a.ncx + (q.parA ? cx1 : cx0));
+                cB = static_cast<int>(base + cyB * a.ncx + (parB ? cx1 : cx0));
+            } else {
+                const uint32_t slotA = uint32_t(colour) * a.nhalf + (q.zP * a.Ly + y2) * hx + kx;
+                const int *cell = a.cell + int64_t(inst) * a.n_inst_sites;
+                cA = cell[slotA];
+                cB = cell[slotA + Ly2 * hx];
+            }
+            const float *sg = a.sigma + hsel;
+            q.sA[0] = __ldg(sg + cA * 4);
+            q.sA[1] = __ldg(sg + cA * 4 + 2);
+            q.sB[0] = __ldg(sg + cB * 4);
+            q.sB[1] = __ldg(sg + cB * 4 + 2);
+        }
+    };
+
+    auto ldpair = [&](uint32_t lo) {        // lo and hi words of a pair in this CTA's shared memory
+        const ulonglong2 l = lds16(lo), h = lds16(lo + hiB);
+        return Pair4{f2{l.x}, f2{l.y}, f2{h.x}, f2{h.y}};
+    };
+    auto ldpeer = [&](uint32_t lo, uint32_t peer) {
+        const ulonglong2 l = ldsc16(peer_addr(lo, peer)), h = ldsc16(peer_addr(lo + hiB, peer));
+        return Pair4{f2{l.x}, f2{l.y}, f2{h.x}, f2{h.y}};
+    };
+
+    // the pass itself, from prepared data
+    auto compute = [&](int t, const Prep &q) {
+        const int P = q.P;
+        const uint32_t Wt = own_base + q.so;
+        const uint32_t Om = oth_base + q.sm, O0 = oth_base + q.s0, Op = oth_base + q.sp;
+        f2 htx{0}, hty{0}, htz{0}, h1x{0}, h1y{0}, h1z{0};
+        // sum order z+1, z-1, y+1, y-1, x, x' (that of checker_pair_kernel)
+        add_neighbour(ldpair(Op + colB), htx, hty, htz, h1x, h1y, h1z);
+        add_neighbour(ldpair(Om + colB), htx, hty, htz, h1x, h1y, h1z);
+        {
+            Pair4 n;
+            if (r + 1 < R) {
+                n = ldpair(O0 + colB + hx * 16u);
+            } else if (g == 0) {
+                const uint32_t h = halo_base + (static_cast<uint32_t>(t) % kSwDH) * 64u * hx + (hx + kx) * 16u;
+                const ulonglong2 l = lds16(h), hh = lds16(h + 32u * hx);
+                n = Pair4{f2{l.x}, f2{l.y}, f2{hh.x}, f2{hh.y}};
+            } else {
+                n = ldpeer(O0 + kx * 16u, peer_up);                  // row 0 of the CTA above
+            }
+            if (y2 + 1 == Ly2) n = swap_lanes(n);
+            add_neighbour(n, htx, hty, htz, h1x, h1y, h1z);
+        }
+        {
+            Pair4 n;
+            if (r > 0) {
+                n = ldpair(O0 + colB - hx * 16u);
+            } else if (g == 0) {
+                const uint32_t h = halo_base + (static_cast<uint32_t>(t) % kSwDH) * 64u * hx + kx * 16u;
+                const ulonglong2 l = lds16(h), hh = lds16(h + 32u * hx);
+                n = Pair4{f2{l.x}, f2{l.y}, f2{hh.x}, f2{hh.y}};
+            } else {
+                n = ldpeer(O0 + ((R - 1) * hx + kx) * 16u, peer_dn);  // last row of the CTA below
+            }
+            if (y2 == 0) n = swap_lanes(n);
+            add_neighbour(n, htx, hty, htz, h1x, h1y, h1z);
+        }
+        add_neighbour(ldpair(O0 + colB), htx, hty, htz, h1x, h1y, h1z);
+        const uint32_t rowB = O0 + r * hx * 16u;
+        const uint32_t parB = q.parA ^ par_flip;
+        if (q.parA == parB) {
+            add_neighbour(ldpair(rowB + (q.parA ? kxp : kxm) * 16u), htx, hty, htz, h1x, h1y, h1z);
+        } else {
+            const Pair4 Pp = ldpair(rowB + kxp * 16u), M = ldpair(rowB + kxm * 16u);
+            const Pair4 &LA = q.parA ? Pp : M, &LB = q.parA ? M : Pp;
+            add_neighbour(Pair4{f2_mix(LA.x, LB.x), f2_mix(LA.y, LB.y), f2_mix(LA.z, LB.z), f2_mix(LA.w, LB.w)}, htx,
+                          hty, htz, h1x, h1y, h1z);
+        }
+        const ulonglong2 olo = lds16(Wt + colB), ohi = lds16(Wt + colB + hiB);
+        f2 sx{olo.x}, sy{olo.y}, sz{ohi.x};
+        const f2 wv{ohi.y};
+        f2 sig{0};
+        if (a.noise) {
+            float wA, wB;
+            f2_split(wv, wA, wB);
+            sig = f2_make(wA != 0.0f ? q.sA[1] : q.sA[0], wB != 0.0f ? q.sB[1] : q.sB[0]);
+        }
+        // the constants are made for dt/2; pass 1 runs for dt (the step-length
+        // terms doubled, exactly as the separate pass's own constants)
+        pair_update<AXZ>(sx, sy, sz, htx, hty, htz, h1x, h1y, h1z, wv, a.noise != 0, sig, q.g1, q.g2, q.g3, a.k,
+                         g == 1);
+        float sA, sB;
+        f2_split(sx + sy + sz, sA, sB);
+        if (!isfinite(sA) || !isfinite(sB)) atomicOr(a.health, kHealthNonFinite);
+        // the result replaces the pair in its tile: for the later passes and
+        // the neighbouring CTAs (passes 0 and 1), and for the bulk store of
+        // the finished plane (passes 1 and 2)
+        sts16(Wt + colB, ulonglong2{sx.v, sy.v});
+        sts16(Wt + colB + hiB, ulonglong2{sz.v, ohi.y});
+    };
+    // thread 0, after the barrier that follows step t: the CTA's rows of the
+    // planes finished in step t -- colour 1 of p0(t) - 2 (pass 1) and colour 0
+    // of p0(t) - 4 (pass 2) -- to the output buffer, by bulk copies (no
+    // generic global stores, so the barriers' release orders shared memory
+    // only); the groups are waited for before their tiles are refilled
+    auto store_finished = [&](int t) {
+        bool any = false;
+        const int P1 = z0 - 4 + t, P2 = z0 - 6 + t;
+        if (t >= 3 && P1 >= z0 && P1 < z1) {
+            const ulonglong2 *src = tile1(P1);
+            ulonglong2 *dst = out + a.nhalf + (zwrap(P1) * Ly2 + y0) * hx;
+            bulk_copy_s2g(dst, src, RH * 16u);
+            bulk_copy_s2g(dst + a.npair, src + RH, RH * 16u);
+            any = true;
+        }
+        if (t >= 6 && P2 >= z0 && P2 < z1) {
+            const ulonglong2 *src = tile0(P2);
+            ulonglong2 *dst = out + (zwrap(P2) * Ly2 + y0) * hx;
+            bulk_copy_s2g(dst, src, RH * 16u);
+            bulk_copy_s2g(dst + a.npair, src + RH, RH * 16u);
+            any = true;
+        }
+        if (any) bulk_commit();
+    };
+
+    auto wait_batch = [&](int u) {
+        if (!mbar_wait(bar + (u % 3), static_cast<uint32_t>(u / 3) & 1u, kBulkWaitNs)) {
+            atomicOr(a.health, kHealthTimeout);
+            s_late = 1;
+        }
+    };
+
+    if (tid == 0) {
+        s_late = 0;
+        for (int i = 0; i < 3; ++i) mbar_init(bar + i, 1);
+        mbar_init_fence();
+        issue(0);
+        if (1 <= last_batch) issue(1);
+    }
+    // the first step of each pass: pass 0 runs step 0 before the loop (and
+    // step t + 1 in iteration t), pass 1 from step 3, pass 2 from step 6
+    const int first = g == 0 ? 0 : (g == 1 ? 3 : 6);
+    const int lastt = g == 0 ? last_batch : (g == 1 ? Z + 4 : Z + 5);
+    Prep q;
+    prepare(first, q, true);
+    __syncthreads();
+    if (g == 0) {
+        wait_batch(0);
+        compute(0, q);
+        if (1 <= lastt) prepare(1, q, false);
+    }
+    cluster_arrive();
+    const int T = Z + 6;
+    for (int t = 0; t < T; ++t) {
+        cluster_wait();                      // every CTA of the cluster finished step t - 1
+        if (tid == 0) {
+            fence_proxy_async_smem();        // the threads' tile writes, before the bulk engine reads them
+            if (t >= 1) store_finished(t - 1);
+            // tiles refilled by this batch were stored (if at all) at least
+            // two steps ago: let all but the newest store group finish reading
+            bulk_wait_read<1>();
+            if (t + 2 <= last_batch) issue(t + 2);
+        }
+        const int mine = g == 0 ? t + 1 : t; // the step this thread's pass runs in this iteration
+        const bool run = mine >= first && mine <= lastt;
+        if (run) {
+            if (g == 0) wait_batch(mine);
+            compute(mine, q);
+        }
+        cluster_arrive();
+        // the next step's noise and amplitudes while the barrier completes
+        if (run && mine + 1 <= lastt) prepare(mine + 1, q, false);
+    }
+    cluster_wait();                          // no CTA leaves while a peer may still read its tiles
+    __syncthreads();
+    if (tid == 0) {
+        fence_proxy_async_smem();
+        store_finished(T - 1);
+        bulk_wait_all();                     // the output is written before the flip below
+        // after a wait that ran out, let the copies still in flight land
+        // (again bounded) before the CTA's shared memory goes away
+        if (s_late)
+            for (int u = max(0, last_batch - 2); u <= last_batch; ++u)
+                mbar_wait(bar + (u % 3), static_cast<uint32_t>(u / 3) & 1u, kBulkWaitNs);
+        __threadfence();
+        if (atomicAdd(w.done, 1u) == w.ctas - 1) {
+            *w.cur = 1 - cur;
+            *w.done = 0u;
+            __threadfence();
+        }
+    }
+}
+
 // Observables of the pair layout: the same per-species partial sums, block
 // by block, as the general observable kernel.  Per site, in FP32 and tesla
 // (the spins are FP32): the unit-free terms s, s.h, (s.n)^2, B.s,
@@ -642,7 +1039,7 @@ __global__ void __launch_bounds__(kObsBlock) checker_pair_obs_kernel(PairArgs a,
 #pragma unroll
         for (int t = 0; t < kObsTerms; ++t) all[t] = one[t] = 0.0;
         int n_all = 0, n_one = 0;
-        const ulonglong2 *base = a.S + int64_t(inst) * a.n_inst_sites;
+        const ulonglong2 *base = pair_state(a) + int64_t(inst) * a.n_inst_sites;
         for (int j = 0; j < kObsSpan / 2 / kObsBlock; ++j) {
             const uint32_t P = local * (kObsSpan / 2) + threadIdx.x + uint32_t(j) * kObsBlock;
             if (P >= 2 * a.npair) break;
@@ -710,11 +1107,12 @@ __global__ void __launch_bounds__(kObsBlock) checker_pair_obs_kernel(PairArgs a,
 
 // pair planes <-> general SoA.  One thread per pair; general slot of a site
 // within its instance: colour * nhalf + (z Ly + y) hx + kx.
-__global__ void pair_to_general_kernel(const float4 *__restrict__ S, float *sx, float *sy, float *sz, int64_t npairs,
-                                       uint32_t hx, uint32_t Ly2, uint32_t npair, const int64_t *step,
-                                       int sample_every, int conditional)
+__global__ void pair_to_general_kernel(const float4 *S0, const float4 *S1, const int *cur, float *sx, float *sy,
+                                       float *sz, int64_t npairs, uint32_t hx, uint32_t Ly2, uint32_t npair,
+                                       const int64_t *step, int sample_every, int conditional)
 {
     if (conditional && (sample_every <= 0 || (*step + 1) % sample_every != 0)) return;
+    const float4 *__restrict__ S = *cur ? S1 : S0;
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= npairs) return;
     const int64_t block = g / npair;              // (instance, colour) block
@@ -733,10 +1131,12 @@ __global__ void pair_to_general_kernel(const float4 *__restrict__ S, float *sx, 
     sz[iB] = hi.y;
 }
 
-__global__ void pair_from_general_kernel(float4 *S, const float *__restrict__ sx, const float *__restrict__ sy,
-                                         const float *__restrict__ sz, const uint8_t *__restrict__ spc,
-                                         int64_t npairs, uint32_t hx, uint32_t Ly2, uint32_t npair)
+__global__ void pair_from_general_kernel(float4 *S0, float4 *S1, const int *cur, const float *__restrict__ sx,
+                                         const float *__restrict__ sy, const float *__restrict__ sz,
+                                         const uint8_t *__restrict__ spc, int64_t npairs, uint32_t hx, uint32_t Ly2,
+                                         uint32_t npair)
 {
+    float4 *S = *cur ? S1 : S0;
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= npairs) return;
     const int64_t block = g / npair;
@@ -1208,6 +1608,10 @@ struct EngineState {
     int n_inst = 0;
     // checker
     void *S = nullptr;
+    void *S1 = nullptr;              // FP32: second state buffer (= S unless the fused sweep is offered)
+    int *cur = nullptr;              // FP32: which of S / S1 holds the current state
+    unsigned *done = nullptr;        // fused sweep: CTAs finished in the running launch
+    SweepShape sweep{};              // fused sweep launch shape (sweep.C == 0: not offered)
     CheckerInst *ci = nullptr;
     int64_t work = 0;
     int K = 2;
@@ -1343,11 +1747,9 @@ PairConsts make_pair_consts(const EngineState *e, const StepParams &p, int hsel)
     k.negpi = host_splat(-M_PI);
     k.s3 = host_splat(-1.0 / 6.0);
     k.s5 = host_splat(1.0 / 120.0);
-    k.s7 = host_splat(-1.0 / 5040.0);
     k.c2 = host_splat(-0.5);
     k.c4 = host_splat(1.0 / 24.0);
     k.c6 = host_splat(-1.0 / 720.0);
-    k.c8 = host_splat(1.0 / 40320.0);
     return k;
 }
 
@@ -1487,6 +1889,76 @@ bool setup_tiled(EngineState *e)
 }
 }  // namespace
 
+// Launch shape of the fused sweep: R = the largest divisor of Ly/2 with
+// R hx <= 256 pair columns (3 R hx threads), clusters of C = Ly/2 / R <= 16
+// CTAs, shared memory for the plane rings, and the number of z segments per
+// instance that minimises (waves of clusters) x (planes per segment + 6).
+bool setup_sweep(EngineState *e)
+{
+    const uint32_t hx = e->shape[0] / 2, Ly2 = e->shape[1] / 2, Lz = e->shape[2];
+    if (e->K != 2 || hx < 1 || Ly2 < 1 || Lz < 4) return false;
+    uint32_t R = 0;
+    for (uint32_t c = std::min<uint32_t>(256 / hx, Ly2); c >= 1; --c)
+        if (Ly2 % c == 0) {
+            R = c;
+            break;
+        }
+    if (R == 0) return false;
+    const uint32_t C = Ly2 / R;
+    if (C > 16) return false;
+    SweepShape sh;
+    sh.R = R;
+    sh.C = C;
+    sh.threads = 3 * R * hx;
+    sh.smem = sweep_smem_bytes(R * hx, hx);
+    if (sh.smem > 227u * 1024u) return false;
+    int nclusters = 0;
+    for (const void *fn : {reinterpret_cast<const void *>(checker_sweep_kernel<true>),
+                           reinterpret_cast<const void *>(checker_sweep_kernel<false>)}) {
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sh.smem)) !=
+                cudaSuccess ||
+            (C > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+            cudaGetLastError();
+            return false;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(C, 1, 1);
+        cfg.blockDim = dim3(sh.threads, 1, 1);
+        cfg.dynamicSmemBytes = sh.smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0, per_sm = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess || n < 1 ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, static_cast<int>(sh.threads), sh.smem) !=
+                cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            return false;
+        }
+        // clusters resident at once: never more than the SMs hold CTAs
+        if (e->sm_count > 0) n = std::min(n, e->sm_count * per_sm / static_cast<int>(C));
+        if (n < 1) return false;
+        nclusters = nclusters == 0 ? n : std::min(nclusters, n);
+    }
+    double best = 0.0;
+    for (uint32_t s = 1; s <= std::max<uint32_t>(1, Lz / 4); ++s) {
+        const uint64_t clusters = uint64_t(s) * e->n_inst;
+        const double waves = double((clusters + nclusters - 1) / nclusters);
+        const double cost = waves * (double((Lz + s - 1) / s) + 6.0);
+        if (best == 0.0 || cost < best) {
+            best = cost;
+            sh.nseg = s;
+        }
+    }
+    e->sweep = sh;
+    return true;
+}
+
 int engine_create(const tts_system_desc &d, const std::vector<HostInstance> &host,
                   const std::vector<std::vector<int64_t>> &slot_of_atom, const std::vector<DevInstance> &dinst,
                   const StepParams &p, const DevBuffers &b, int engine, cudaStream_t st, EngineState **out)
@@ -1582,11 +2054,25 @@ int engine_create(const tts_system_desc &d, const std::vector<HostInstance> &hos
             if (setup_tiled(e)) e->configs.push_back({0, 0});
         }
         const size_t vs = d.precision == 64 ? sizeof(double4a) : sizeof(float4);
+        const bool sweep = e->pair && setup_sweep(e);
         if ((ce = cudaMalloc(&e->S, size_t(e->n_total) * vs)) != cudaSuccess ||
-            (ce = cudaMalloc(reinterpret_cast<void **>(&e->ci), ci.size() * sizeof(CheckerInst))) != cudaSuccess) {
+            (ce = cudaMalloc(reinterpret_cast<void **>(&e->ci), ci.size() * sizeof(CheckerInst))) != cudaSuccess ||
+            (ce = cudaMalloc(reinterpret_cast<void **>(&e->cur), sizeof(int))) != cudaSuccess ||
+            (sweep && (ce = cudaMalloc(&e->S1, size_t(e->n_total) * vs)) != cudaSuccess) ||
+            (sweep && (ce = cudaMalloc(reinterpret_cast<void **>(&e->done), sizeof(unsigned))) != cudaSuccess)) {
             cudaGetLastError();
             engine_destroy(e);
             return eng_fail(TTS_ERR_OOM, std::string("checker buffers: ") + cudaGetErrorString(ce));
+        }
+        cudaMemsetAsync(e->cur, 0, sizeof(int), st);
+        if (sweep) {
+            cudaMemsetAsync(e->done, 0, sizeof(unsigned), st);
+            // offered to the autotuner; the separate passes stay the default
+            // (on 128^3 x 4 they measured about twice as fast: the fused
+            // launch is bound by the latency of one update a warp per step)
+            e->configs.push_back({-2, 0});
+        } else {
+            e->S1 = e->S;
         }
         cudaMemcpyAsync(e->ci, ci.data(), ci.size() * sizeof(CheckerInst), cudaMemcpyHostToDevice, st);
         if ((ce = engine_sync_from_general(e, b, st)) != cudaSuccess || (ce = cudaStreamSynchronize(st)) != cudaSuccess) {
@@ -1672,6 +2158,9 @@ int engine_create(const tts_system_desc &d, const std::vector<HostInstance> &hos
 void engine_destroy(EngineState *e)
 {
     if (!e) return;
+    if (e->S1 && e->S1 != e->S) cudaFree(e->S1);
+    for (void *q : {static_cast<void *>(e->cur), static_cast<void *>(e->done)})
+        if (q) cudaFree(q);
     for (void *q : {e->S, static_cast<void *>(e->ci), static_cast<void *>(e->ri), static_cast<void *>(e->order),
                     static_cast<void *>(e->queue), e->traj_sig, static_cast<void *>(e->traj_T),
                     static_cast<void *>(e->open_state)})
@@ -1705,11 +2194,26 @@ void engine_set_config(EngineState *e, int index)
 }
 
 namespace {
+// Block shape (pairs or sites along x, rows) of the separate-pass kernels;
+// with the fused sweep selected (bx < 0) the merged sweep's passes run
+// checker_pair_kernel on its default shape.
+void row_block(const EngineState *e, int &bx, int &by)
+{
+    bx = e->bx;
+    by = e->by;
+    if (bx < 0) {
+        bx = e->shape[0] / 2 >= 64 ? 64 : 32;
+        by = 128 / bx;
+    }
+}
+
 // Launch arguments of the FP32 pair kernels for a pass with step h(hsel).
 PairArgs pair_args(const EngineState *e, const StepParams &p, const DevBuffers &b, int hsel)
 {
     PairArgs a{};
     a.S = static_cast<ulonglong2 *>(e->S);
+    a.S1 = static_cast<ulonglong2 *>(e->S1);
+    a.cur = e->cur;
     a.cell = b.cell;
     a.sigma = static_cast<const float *>(b.sigma);
     a.step = b.step;
@@ -1721,7 +2225,11 @@ PairArgs pair_args(const EngineState *e, const StepParams &p, const DevBuffers &
     a.Lz = e->shape[2];
     a.hx = e->shape[0] / 2;
     a.Ly2 = e->shape[1] / 2;
-    a.nkx = e->bx ? (a.hx + e->bx - 1) / e->bx : 0;
+    {
+        int bx, by;
+        row_block(e, bx, by);
+        a.nkx = bx ? (a.hx + bx - 1) / bx : 0;
+    }
     a.nhalf = static_cast<uint32_t>(e->n_total / e->n_inst / 2);
     a.npair = a.nhalf / 2;
     a.n_inst_sites = e->n_total / e->n_inst;
@@ -1761,7 +2269,8 @@ void launch_pair_to_general(EngineState *e, const DevBuffers &b, cudaStream_t st
     const int bs = 256;
     const int64_t np = e->n_total / 2;
     pair_to_general_kernel<<<(np + bs - 1) / bs, bs, 0, st>>>(
-        static_cast<const float4 *>(e->S), static_cast<float *>(b.sx), static_cast<float *>(b.sy),
+        static_cast<const float4 *>(e->S), static_cast<const float4 *>(e->S1), e->cur, static_cast<float *>(b.sx),
+        static_cast<float *>(b.sy),
         static_cast<float *>(b.sz), np, e->shape[0] / 2, e->shape[1] / 2,
         static_cast<uint32_t>(e->n_total / e->n_inst / 4), b.step, sample_every, conditional);
 }
@@ -1807,12 +2316,40 @@ cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuf
         w.sample_every = p.sample_every;
         return w;
     };
-    for (int pass = 0; pass < npass && err == cudaSuccess; ++pass) {
+    const bool fused = e->pair && e->bx == -2 && !p.merged;
+    if (fused && err == cudaSuccess) {
+        // the three passes of the step in one launch (checker_sweep_kernel)
+        PairArgs a = pair_args(e, p, b, 0);
+        SweepArgs w{};
+        w.R = e->sweep.R;
+        w.nseg = e->sweep.nseg;
+        w.done = e->done;
+        w.ctas = e->sweep.C * e->sweep.nseg * static_cast<uint32_t>(e->n_inst);
+        w.cur = e->cur;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(e->sweep.C, e->sweep.nseg, e->n_inst);
+        cfg.blockDim = dim3(e->sweep.threads, 1, 1);
+        cfg.dynamicSmemBytes = e->sweep.smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = e->sweep.C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        err = e->axis_z ? cudaLaunchKernelEx(&cfg, checker_sweep_kernel<true>, a, w)
+                        : cudaLaunchKernelEx(&cfg, checker_sweep_kernel<false>, a, w);
+        ++*kernels;
+    }
+    for (int pass = 0; pass < npass && err == cudaSuccess && !fused; ++pass) {
         const int c = pass < e->K - 1 ? pass : (pass == e->K - 1 ? e->K - 1 : 2 * e->K - 2 - pass);
         const int hsel = pass == e->K - 1 ? 1 : 0;
-        const dim3 block(e->bx, e->by);
-        const uint32_t nkx = e->bx ? (e->shape[0] / 2 + e->bx - 1) / e->bx : 0;
-        const dim3 grid(e->by ? nkx * ((e->shape[1] + e->by - 1) / e->by) : 0, e->shape[2], e->n_inst);
+        int rbx, rby;
+        row_block(e, rbx, rby);
+        const dim3 block(rbx, rby);
+        const uint32_t nkx = rbx ? (e->shape[0] / 2 + rbx - 1) / rbx : 0;
+        const dim3 grid(rby ? nkx * ((e->shape[1] + rby - 1) / rby) : 0, e->shape[2], e->n_inst);
         auto fill_shape = [&](auto &a) {
             a.nkx = nkx;
             a.Lx = e->shape[0];
@@ -1851,7 +2388,7 @@ cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuf
                                     : (sw ? checker_pair_tiled_kernel<false, true> : checker_pair_tiled_kernel<false, false>);
                 fn<<<e->tile_grid, 256, e->tile_smem, st>>>(a, e->tile, c, hsel, pass);
             } else {
-                const dim3 pgrid(a.nkx * ((a.Ly2 + e->by - 1) / e->by), e->shape[2], e->n_inst);
+                const dim3 pgrid(a.nkx * ((a.Ly2 + rby - 1) / rby), e->shape[2], e->n_inst);
                 auto fn = e->axis_z ? (sw ? checker_pair_kernel<true, true> : checker_pair_kernel<true, false>)
                                     : (sw ? checker_pair_kernel<false, true> : checker_pair_kernel<false, false>);
                 if (sw) {
@@ -2024,7 +2561,8 @@ cudaError_t engine_sync_from_general(EngineState *e, const DevBuffers &b, cudaSt
     else {
         const int64_t np = e->n_total / 2;
         pair_from_general_kernel<<<(np + bs - 1) / bs, bs, 0, st>>>(
-            static_cast<float4 *>(e->S), static_cast<const float *>(b.sx), static_cast<const float *>(b.sy),
+            static_cast<float4 *>(e->S), static_cast<float4 *>(e->S1), e->cur, static_cast<const float *>(b.sx),
+            static_cast<const float *>(b.sy),
             static_cast<const float *>(b.sz), b.species, np, e->shape[0] / 2, e->shape[1] / 2,
             static_cast<uint32_t>(e->n_total / e->n_inst / 4));
     }
