@@ -103,6 +103,19 @@ __device__ __forceinline__ float lg2_approx(float x)
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+// sine and cosine of an angle in (-pi, pi), the hardware approximations
+__device__ __forceinline__ float sin_approx(float x)
+{
+    float r;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float cos_approx(float x)
+{
+    float r;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 // lane-wise transcendental of an f2
 template <float (*Fn)(float)>
 __device__ __forceinline__ f2 f2_map(f2 a)
@@ -129,8 +142,8 @@ struct PairConsts {
     f2 u_off;          // uniform = (1 + (k >> 9) 2^-23) + u_off, u_off = 2^-24 - 1 (exact)
     f2 m2ln2;          // -2 ln 2   (-2 ln u = -2 ln2 log2 u)
     f2 twopi, negpi;
-    f2 s3, s5, s7;     // sine Taylor coefficients -1/6, 1/120, -1/5040
-    f2 c2, c4, c6, c8; // cosine Taylor coefficients -1/2, 1/24, -1/720, 1/40320
+    f2 s3, s5;         // sine Taylor coefficients -1/6, 1/120
+    f2 c2, c4, c6;     // cosine Taylor coefficients -1/2, 1/24, -1/720
 };
 
 // Thermal-field directions of two sites: one Philox4x32-10 block per site,
@@ -154,15 +167,9 @@ __device__ __forceinline__ void pair_noise(const u32x4 &ctrA, const u32x4 &ctrB,
     const f2 nr23 = (l2 * f2_map<rsqrt_approx>(l2)) * k.neg1;
     const f2 a1 = fma2(u1, k.twopi, k.negpi);
     const f2 a3 = fma2(u3, k.twopi, k.negpi);
-    float a1A, a1B, a3A, a3B;
-    f2_split(a1, a1A, a1B);
-    f2_split(a3, a3A, a3B);
-    float s1A, c1A, s1B, c1B;
-    __sincosf(a1A, &s1A, &c1A);
-    __sincosf(a1B, &s1B, &c1B);
-    g1 = nr01 * f2_make(c1A, c1B);
-    g2 = nr01 * f2_make(s1A, s1B);
-    g3 = nr23 * f2_make(__cosf(a3A), __cosf(a3B));
+    g1 = nr01 * f2_map<cos_approx>(a1);
+    g2 = nr01 * f2_map<sin_approx>(a1);
+    g3 = nr23 * f2_map<cos_approx>(a3);
 }
 
 // Two sites of one colour.  s = (x, y, z) of lanes A and B, ht / h1 the sums
@@ -235,18 +242,23 @@ __device__ __forceinline__ void pair_update(f2 &sx, f2 &sy, f2 &sz, f2 htx, f2 h
     const f2 iD = f2_map<rcp_approx>(opc + omcE);
     const f2 cp = (opc - omcE) * iD;
     const f2 rho = (em + em) * iD;
-    // sin / cos of phi: Taylor through phi^7 / phi^8 below 0.25 rad
+    // sin / cos of phi: Taylor through phi^5 / phi^6 below 1/16 rad (the
+    // truncation, below phi^7 / 5040, is under 1e-11 relative); the usual
+    // sub-step angle is ~0.01 rad
     const f2 p2 = phi * phi;
-    f2 sn = phi * fma2(p2, fma2(p2, fma2(p2, k.s7, k.s5), k.s3), k.one);
-    f2 cs = fma2(p2, fma2(p2, fma2(p2, fma2(p2, k.c8, k.c6), k.c4), k.c2), k.one);
-    float phA, phB;
+    f2 sn = phi * fma2(p2, fma2(p2, k.s5, k.s3), k.one);
+    f2 cs = fma2(p2, fma2(p2, fma2(p2, k.c6, k.c4), k.c2), k.one);
+    float phA, phB, b2A, b2B;
     f2_split(phi, phA, phB);
-    if (!(phA < 0.25f) || !(phB < 0.25f)) {
+    f2_split(B2, b2A, b2B);
+    // one rarely taken branch for a large angle or a vanishing field in either lane
+    const bool slow = !(phA < 0.0625f && phB < 0.0625f && b2A > 1e-30f && b2B > 1e-30f);
+    if (slow) {
         float snA, snB, csA, csB;
         f2_split(sn, snA, snB);
         f2_split(cs, csA, csB);
-        if (!(phA < 0.25f)) sincosf(phA, &snA, &csA);
-        if (!(phB < 0.25f)) sincosf(phB, &snB, &csB);
+        if (!(phA < 0.0625f)) sincosf(phA, &snA, &csA);
+        if (!(phB < 0.0625f)) sincosf(phB, &snB, &csB);
         sn = f2_make(snA, snB);
         cs = f2_make(csA, csB);
     }
@@ -256,17 +268,16 @@ __device__ __forceinline__ void pair_update(f2 &sx, f2 &sy, f2 &sz, f2 htx, f2 h
     const f2 oz = fma2(rbq, qz, fma2(ra, pz, cp * bz));
     const f2 on = f2_map<rsqrt_approx>(fma2(oz, oz, fma2(oy, oy, ox * ox)));
     f2 nx_ = ox * on, ny_ = oy * on, nz_ = oz * on;
-    // a lane with no field (|B| = 0) keeps its spin
-    float b2A, b2B;
-    f2_split(B2, b2A, b2B);
-    if (!(b2A > 0.0f) || !(b2B > 0.0f)) {
+    // a lane with no field (|B|^2 <= 1e-30 T^2: the precession angle of a
+    // sub-step is below 1e-20 rad) keeps its spin
+    if (slow) {
         float oA, oB, nA, nB;
         f2 *outs[3] = {&nx_, &ny_, &nz_};
         const f2 ins[3] = {sx, sy, sz};
         for (int j = 0; j < 3; ++j) {
             f2_split(ins[j], oA, oB);
             f2_split(*outs[j], nA, nB);
-            *outs[j] = f2_make(b2A > 0.0f ? nA : oA, b2B > 0.0f ? nB : oB);
+            *outs[j] = f2_make(b2A > 1e-30f ? nA : oA, b2B > 1e-30f ? nB : oB);
         }
     }
     sx = nx_;
