@@ -114,4 +114,4 @@ def test_merged_two_spin_thermal_law():
     per_pair = _time_average(o, 6 * nt, 20, nt // 2, dots)
     m = per_pair.mean()
     se = per_pair.std(ddof=1) / np.sqrt(npair)
-    assert abs(m - langevin(betaJ)) < 4 * se, (m, langevin(betaJ), se)
+    assert abs(m - langevin(betaJ)) < 3 * se, (m, langevin(betaJ), se)

@@ -2,7 +2,9 @@
 1/sqrt(mu) scaling (Sec. II.C), the placement of (1 + alpha^2) and the
 Stratonovich reading.  Each run averages many independent spins or pairs;
 standard errors come from per-spin (per-pair) time averages, which are
-independent of each other."""
+independent of each other.  Pass rule: within 3 standard errors (a correct
+sampler fails one such check with probability 0.27 %; the seeds are fixed, so
+the outcome is reproducible)."""
 import numpy as np
 import pytest
 
@@ -45,7 +47,7 @@ def test_single_spin_langevin_law(mu, alpha):
     m = per_spin.mean()
     se = per_spin.std(ddof=1) / np.sqrt(per_spin.size)
     x = mu * MUB * B / (KB * T)
-    assert abs(m - langevin(x)) < 4 * se, (m, langevin(x), se)
+    assert abs(m - langevin(x)) < 3 * se, (m, langevin(x), se)
 
 
 def test_two_spin_thermal_law():
@@ -69,7 +71,7 @@ def test_two_spin_thermal_law():
     per_pair = _time_average(o, 6 * nt, 20, nt // 2, dots)
     m = per_pair.mean()
     se = per_pair.std(ddof=1) / np.sqrt(npair)
-    assert abs(m - langevin(betaJ)) < 4 * se, (m, langevin(betaJ), se)
+    assert abs(m - langevin(betaJ)) < 3 * se, (m, langevin(betaJ), se)
 
 
 def _sublattice_temperatures(noise_mu_power):
@@ -93,7 +95,7 @@ def test_mu_fdt_equilibrates_both_sublattices():
     # sum |s x H|^2 / (2 k_B sum s.H) per sublattice)
     Ts, se = _sublattice_temperatures(0.5)
     for k in range(2):
-        assert abs(Ts[k] - 300.0) < max(4 * se[k], 0.03 * 300.0), (Ts, se)
+        assert abs(Ts[k] - 300.0) < 3 * se[k], (Ts, se)
 
 
 def test_without_mu_fdt_heavy_sublattice_runs_cold():
@@ -186,4 +188,4 @@ def test_three_spin_thermal_equilibrium():
     m = per_tri.mean(0)
     se = per_tri.std(0, ddof=1) / np.sqrt(ntri)
     want = np.array(_triangle_quadrature((bJ, bJ, bJ), bK, bB))
-    assert np.all(np.abs(m - want) < 4 * se), (m, want, se)
+    assert np.all(np.abs(m - want) < 3 * se), (m, want, se)
