@@ -254,6 +254,29 @@ TTS_API int tts_step(tts_system *sys, int64_t nsteps);
  * out; the kernel that waited returned early), TTS_ERR_CUDA. */
 TTS_API int tts_sync(tts_system *sys);
 
+/* Bits of the device health word (tts_health).  A kernel that meets one of
+ * these conditions sets its bit and goes on (no trap, no abort); tts_sync
+ * turns a set word into a status, the bits checked in this order. */
+#define TTS_HEALTH_NONFINITE 1u    /* a spin component became NaN or infinite */
+#define TTS_HEALTH_TIMEOUT 2u      /* a bounded device-side wait ran out */
+#define TTS_HEALTH_SKIN 4u         /* moving lattice: an atom moved beyond half the skin */
+#define TTS_HEALTH_COLOUR 8u       /* moving lattice: two exchange-coupled atoms share a colour */
+#define TTS_HEALTH_OVERFLOW 16u    /* moving lattice: more exchange neighbours than the table holds */
+
+/* The device health word as it stands (synchronises; TTS_HEALTH_* bits, 0 =
+ * no fault).  The paper has no counterpart.  Errors: TTS_ERR_ARG, TTS_ERR_CUDA. */
+TTS_API int tts_health(tts_system *sys, unsigned *bits);
+
+/* Self-test of the device's bounded waits, the paper has no counterpart: a
+ * one-CTA kernel on the system's stream waits on a shared-memory barrier for
+ * a transfer that is never issued, with the library's bounded wait cut to
+ * limit_ns; when the wait runs out the kernel sets TTS_HEALTH_TIMEOUT in the
+ * system's health word and returns (no trap), so that the next tts_sync
+ * reports TTS_ERR_DEVICE_TIMEOUT and the context stays usable.  The flag then
+ * stays set like any other fault.  Asynchronous.  Errors: TTS_ERR_ARG
+ * (limit_ns outside (0, 10 s]), TTS_ERR_CUDA. */
+TTS_API int tts_selftest_wait(tts_system *sys, int64_t limit_ns);
+
 /* Copy up to max_samples observable records of one instance, oldest first,
  * TTS_NOBS doubles each.  These are the quantities the paper follows: the
  * sublattice magnetisations whose z components define switching (Sec. II.G),

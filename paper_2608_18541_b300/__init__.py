@@ -116,7 +116,11 @@ _SIG = {
     "tts_get_velocities": [C.c_void_p, C.c_int, _P(C.c_double)],
     "tts_ttm_advance_noalloc": [_P(tts_ttm_desc), _P(C.c_double), C.c_double, C.c_int64, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p],
+    "tts_health": [C.c_void_p, _P(C.c_uint)],
+    "tts_selftest_wait": [C.c_void_p, C.c_int64],
 }
+
+HEALTH = {"nonfinite": 1, "timeout": 2, "skin": 4, "colour": 8, "overflow": 16}
 
 _LIB = None
 
@@ -256,6 +260,7 @@ class System:
         _check(L.tts_create_system(C.byref(d), C.c_void_p(stream or 0), C.byref(h)))
         self._h = h
         self.precision = precision
+        self.ttm_cells = 0                 # cells of every instance's TTM grid (0: none)
         info = self.info()
         self.n_total = info.n_total
         self.n_instances = info.n_instances
@@ -282,6 +287,7 @@ class System:
     def set_ttm_grid(self, ttm):
         t = make_ttm(ttm)
         _check(load().tts_set_ttm_grid(self._h, C.byref(t)))
+        self.ttm_cells = int(t.cells[0]) * int(t.cells[1]) * int(t.cells[2])
 
     def step(self, n):
         _check(load().tts_step(self._h, int(n)))
@@ -348,7 +354,10 @@ class System:
         return out
 
     def get_ttm(self, inst=0, ncells=None):
-        nc = ncells or 1
+        # tts_get_ttm writes every cell of the instance's grid
+        nc = max(self.ttm_cells, 1)
+        if ncells is not None and ncells != nc:
+            raise ValueError("the grid has %d cells, not %d" % (nc, ncells))
         Te = np.empty(nc)
         Tl = np.empty(nc)
         P0 = C.c_double()
@@ -423,6 +432,16 @@ class System:
 
     def profile_enable(self, on=True):
         _check(load().tts_profile_enable(self._h, 1 if on else 0))
+
+    def health(self):
+        """tts_health: the raw device health word (TTS_HEALTH_* bits, see HEALTH)."""
+        b = C.c_uint()
+        _check(load().tts_health(self._h, C.byref(b)))
+        return b.value
+
+    def selftest_wait(self, limit_ns):
+        """tts_selftest_wait: a bounded device wait that is made to run out."""
+        _check(load().tts_selftest_wait(self._h, int(limit_ns)))
 
     def profile_read(self):
         ms = C.c_double()

@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "tts_bulk.cuh"
 #include "tts_engines.h"
 #include "tts_internal.h"
 #include "tts_kernels.h"
@@ -1373,6 +1374,43 @@ int tts_set_step(tts_system *s, int64_t step)
     TTS_CUDA(cudaMemcpy(s->b.step, &step, sizeof(int64_t), cudaMemcpyHostToDevice), "write step");
     TTS_CUDA(cudaMemset(s->b.open, 0, sizeof(int)), "reset sweep state");
     s->host_step = step;
+    return TTS_OK;
+}
+
+static_assert(kHealthNonFinite == TTS_HEALTH_NONFINITE && kHealthTimeout == TTS_HEALTH_TIMEOUT &&
+                  kHealthSkin == TTS_HEALTH_SKIN && kHealthColour == TTS_HEALTH_COLOUR &&
+                  kHealthOverflow == TTS_HEALTH_OVERFLOW,
+              "device health bits and their ABI values");
+
+int tts_health(tts_system *s, unsigned *bits)
+{
+    if (!s || !bits) return fail(TTS_ERR_ARG, "null argument");
+    TTS_CUDA(cudaStreamSynchronize(s->stream), "synchronise");
+    TTS_CUDA(cudaMemcpy(bits, s->b.health, sizeof(unsigned), cudaMemcpyDeviceToHost), "read health");
+    return TTS_OK;
+}
+
+namespace {
+// A wait that no transfer completes: the barrier expects 16 bytes that are
+// never sent, so the bounded wait runs out and the kernel reports it.
+__global__ void selftest_wait_kernel(unsigned *health, uint64_t limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+    mbar_arrive_expect_tx(&bar, 16u);
+    if (!mbar_wait(&bar, 0u, limit_ns)) atomicOr(health, kHealthTimeout);
+}
+}  // namespace
+
+int tts_selftest_wait(tts_system *s, int64_t limit_ns)
+{
+    if (!s) return fail(TTS_ERR_ARG, "null system");
+    if (!(limit_ns > 0 && limit_ns <= 10000000000ll)) return fail(TTS_ERR_ARG, "limit must be in (0, 10 s]");
+    selftest_wait_kernel<<<1, 32, 0, s->stream>>>(s->b.health, static_cast<uint64_t>(limit_ns));
+    ++s->launches;
+    TTS_CUDA(cudaGetLastError(), "self-test launch");
     return TTS_OK;
 }
 
