@@ -1052,8 +1052,16 @@ static void wrap_positions(orc_sys *S)
         }
 }
 
+static int finite_pos(const orc_sys *S, int i)
+{
+    return isfinite(S->pos[3 * i]) && isfinite(S->pos[3 * i + 1]) && isfinite(S->pos[3 * i + 2]);
+}
+
 /* all j != i with minimum-image distance below rc, ascending j, as CSR; cell
- * list with cells no smaller than rc (brute force when fewer than 3 cells) */
+ * list with cells no smaller than rc (brute force when fewer than 3 cells).
+ * Atoms whose position is not finite (a run that has blown up) take part in
+ * no pair, so that the state stays inspectable instead of every pair
+ * qualifying. */
 static void pairs_within(const orc_sys *S, double rc, int **pstart, int **pj)
 {
     int n = S->n;
@@ -1073,6 +1081,7 @@ static void pairs_within(const orc_sys *S, double rc, int **pstart, int **pj)
         for (int c = 0; c < nc[0] * nc[1] * nc[2]; ++c) head[c] = -1;
         for (int i = n - 1; i >= 0; --i) {
             int cc[3];
+            if (!finite_pos(S, i)) { next[i] = -1; cellof[3 * i] = -1; continue; }
             for (int k = 0; k < 3; ++k) {
                 cc[k] = (int)floor(S->pos[3 * i + k] / S->box[k] * nc[k]);
                 if (cc[k] >= nc[k]) cc[k] = nc[k] - 1;
@@ -1087,9 +1096,11 @@ static void pairs_within(const orc_sys *S, double rc, int **pstart, int **pj)
     int tcap = 64, *tmp = malloc(sizeof(int) * tcap);
     for (int i = 0; i < n; ++i) {
         int cnt = 0;
-        if (brute) {
+        if (!finite_pos(S, i)) {
+            /* an atom whose position is not finite has no neighbours */
+        } else if (brute) {
             for (int j = 0; j < n; ++j) {
-                if (j == i) continue;
+                if (j == i || !finite_pos(S, j)) continue;
                 double d[3];
                 min_image(S, i, j, d);
                 if (sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) >= rc) continue;
