@@ -136,7 +136,7 @@ def _traffic(kernel, precision):
     return e["bytes_per_launch"] if h.hexdigest()[:16] == e.get("sources_sha") else None
 
 
-def ensemble_leg(P, W, stream, steps=200, sample=8):
+def ensemble_leg(P, W, stream, steps=200, sample=64):
     """Batched FP32 ensemble (1024 GdFeCo instances of uneven size in one
     persistent launch per call) against the plain FP64 path that advances one
     instance per launch sequence, on the same GPU."""

@@ -46,3 +46,43 @@ def test_fp32_ensemble_matches_fp64_oracle_ensemble():
     assert (z > 5).sum() == 0, z
     # the pulse really demagnetised the system (a non-trivial comparison)
     assert mo[:, 0].min() < 0.9 * mo[0, 0]
+
+
+def _oracle_mz(args):
+    s, t, r = args
+    o = O.Oracle(s, t, instance=r, index=r)
+    o.step(STEPS)
+    return o.samples()[:, [3, 6]]
+
+
+def test_phase_diagram_subset_matches_fp64_oracle_ensemble():
+    """Two grid points of the 8 x 8 phase-diagram ensemble (peak T_e 1000 K
+    and 3000 K, 25 fs pulses), 16 realisations each, with the ensemble's own
+    uneven sizes (L ~ U{12..24}) and Gd fractions, on the batched resident
+    engine in FP32 against the FP64 oracle.  Rule: over 20 sample times x 2
+    sublattices x 2 grid points, at most two points beyond 3 SE and none beyond
+    5 SE."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    full, t = W.config_ensemble()
+    picks = [(iT, 0) for iT in (0, 7)]                     # (peak index, duration index)
+    inst = [full["instances"][(iT * 8 + iD) * 16 + r] for iT, iD in picks for r in range(16)]
+    s = dict(full, instances=inst, sample_every=EVERY)
+    g = P.System(s, t, precision=32, engine="resident", instance_base=5000)
+    assert g.engine == "resident"
+    g.step(STEPS)
+    gm = np.array([g.observables(i)[:, [3, 6]] for i in range(len(inst))])
+    with ProcessPoolExecutor(max_workers=8, mp_context=mp.get_context("spawn")) as ex:
+        om = np.array(list(ex.map(_oracle_mz, [(s, t, r) for r in range(len(inst))])))
+    assert gm.shape == om.shape == (32, STEPS // EVERY, 2)
+    bad3 = bad5 = 0
+    for k in range(2):
+        a, b = gm[16 * k:16 * (k + 1)], om[16 * k:16 * (k + 1)]
+        se = np.sqrt(a.var(0, ddof=1) / 16 + b.var(0, ddof=1) / 16)
+        z = np.abs(a.mean(0) - b.mean(0)) / np.maximum(se, 1e-12)
+        bad3 += int((z > 3).sum())
+        bad5 += int((z > 5).sum())
+        # each pulse demagnetised the Fe sublattice (a non-trivial comparison)
+        assert b.mean(0)[:, 0].min() < 0.95 * b.mean(0)[0, 0]
+    assert bad3 <= 2 and bad5 == 0, (bad3, bad5)
