@@ -203,6 +203,48 @@ def merged_leg(P, sysd, ttm, args, stream, spins):
             "note": "sweep closed at every sampling step (once per chunk) and at the end of every call"}
 
 
+def fused_leg(P, g, args, stream, spins, peak, peak_kind):
+    """The same system with the fused symmetric sweep (checker_sweep_kernel:
+    the three colour passes of a step in one launch, the last launch
+    configuration the FP32 checker engine offers): its whole-step rate, the
+    roofline of its launch, and the DRAM traffic of one launch when the ncu
+    record matches the sources.  Bitwise the same spins as the headline's
+    separate passes; reported beside it."""
+    import torch
+    cur, n = g.set_config(-1)
+    if g.engine != "checker" or args.precision != 32 or n < 2:
+        return None
+    g.set_config(n - 1)
+    # the fused configuration launches one spin kernel a step instead of three
+    a = g.info().kernel_launches
+    g.profile_enable(True)
+    g.step(args.chunk)
+    g.sync()
+    kms, ksteps, kss = g.profile_read()
+    g.profile_enable(False)
+    per_step = (g.info().kernel_launches - a) / args.chunk
+    steps = max(1, min(args.steps, 5))
+    g.step(args.chunk)
+    g.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        g.step(args.chunk)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    g.set_config(cur)
+    bpu = BYTES_PER_SPIN_STEP[args.precision]
+    achieved = bpu * kss / (kms / 1e3) / 1e9
+    return {"value": spins * steps * args.chunk / (ms / 1e3), "unit": "spin-steps/s", "ms_per_step": ms / steps,
+            "steps": steps, "kernels_per_dt": per_step, "config": n - 1,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "traffic": _traffic("step_checker_sweep", args.precision),
+                         "kernel": "checker_sweep_kernel", "bytes_per_unit": bpu, "units_per_launch": spins,
+                         "avg_launch_ms": kms / max(ksteps, 1)}}
+
+
 # ---------------------------------------------------------------------------
 # The FP64 CPU oracle on the host cores, the paper's task-level strategy: one
 # single-threaded process per realisation, all running at once.  Everything
@@ -376,6 +418,9 @@ def main():
                     help="steps of realisation 0 compared with the FP64 oracle (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-single", action="store_true", help="skip the single-instance roofline legs")
+    ap.add_argument("--no-fused", action="store_true", help="skip the fused-sweep leg")
+    ap.add_argument("--config", type=int, default=-1,
+                    help="launch configuration of the timed system (tts_set_config index; -1: the default)")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-merged", action="store_true")
     args = ap.parse_args()
@@ -409,6 +454,8 @@ def main():
     g = P.System(sysd, ttm, precision=args.precision, engine=args.engine, stream=stream.cuda_stream,
                  instance_base=rank * n_inst_local)
     spins = g.n_total
+    if args.config >= 0:
+        g.set_config(args.config)
     initial = g.get_state()
     for _ in range(args.warmup):
         g.step(args.chunk)
@@ -509,6 +556,9 @@ def main():
     ens = None
     if world == 1 and not args.no_ensemble:
         ens = ensemble_leg(P, W, stream)
+    fused = None
+    if world == 1 and not args.no_fused:
+        fused = fused_leg(P, g, args, stream, spins, peak, peak_kind)
     single = None
     if world == 1 and not args.no_single and args.workload == "gdfeco_128x4":
         single = [single_leg(P, W, n, args, stream, peak, peak_kind) for n in (128, 256)]
@@ -539,7 +589,8 @@ def main():
                    "engine": engine, "l2": "state and tables exceed L2 (126 MB) per step" if spins * 16 > 126e6
                    else "working set may fit L2", "parallelism": "instances sharded, dp%d" % world},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-        "clocks": clocks, "parity": parity, "single_instance": single, "ensemble": ens, "merged_sweep": merged,
+        "clocks": clocks, "parity": parity, "single_instance": single, "fused_sweep": fused, "ensemble": ens,
+        "merged_sweep": merged,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
