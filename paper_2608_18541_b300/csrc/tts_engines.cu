@@ -79,6 +79,7 @@ struct CheckerArgs {
     uint32_t key0, key1;
     uint32_t Lx, Ly, Lz, hx;     // shape shared by all instances
     uint32_t nkx;                // blocks along the hx colour sites of a row
+    FastDiv dnkx;                // division by nkx (by 1 where nkx = 0)
     uint32_t nhalf;              // sites per colour
     int64_t n_inst_sites;        // sites per instance
     uint32_t inst_base;          // global id of instance 0
@@ -186,6 +187,7 @@ struct PairArgs {
     PhiloxRoundKeys rk;
     uint32_t Lx, Ly, Lz, hx, Ly2;
     uint32_t nkx;                // blocks along the hx colour sites of a row
+    FastDiv dnkx;                // division by nkx (by 1 where nkx = 0)
     uint32_t nhalf;              // sites per colour
     uint32_t npair;              // pairs per colour (nhalf / 2)
     int64_t n_inst_sites;
@@ -304,9 +306,42 @@ __device__ __forceinline__ void neighbour_sums(const PairSite &p, uint32_t hx, u
     }
 }
 
+// How a pair kernel finds the TTM cell of a site: from the cell map, from the
+// coordinates by shifts (every L_k / n_k a power of two) or by invariant
+// division, fixed at launch; or chosen per site at run time.
+enum PairCellMode { kCellMap = 0, kCellShift = 1, kCellDiv = 2, kCellAny = 3 };
+
+// TTM cells of the two sites of a pair.
+template <int CM>
+__device__ __forceinline__ void pair_cells(const PairArgs &a, const PairSite &p, int colour, int &cA, int &cB)
+{
+    if (CM == kCellMap || (CM == kCellAny && !a.cell_formula)) {
+        // general slots of the two sites within the instance
+        const uint32_t slotA = uint32_t(colour) * a.nhalf + (p.z * a.Ly + p.y2) * a.hx + p.kx;
+        const uint32_t slotB = slotA + a.Ly2 * a.hx;
+        const int *cell = a.cell + int64_t(p.inst) * a.n_inst_sites;
+        cA = cell[slotA];
+        cB = cell[slotB];
+        return;
+    }
+    // c_k = floor(k n_k / L_k)
+    auto cc = [&](uint32_t v, uint32_t n, const FastDiv &d, int sh) {
+        if (CM == kCellShift) return v >> sh;
+        if (CM == kCellDiv) return fast_div(v * n, d);
+        return sh >= 0 ? v >> sh : fast_div(v * n, d);
+    };
+    const uint32_t cz = cc(p.z, a.ncz, a.dLz, a.shz);
+    const uint32_t cyA = cc(p.y2, a.ncy, a.dLy, a.shy), cyB = cc(p.y2 + a.Ly2, a.ncy, a.dLy, a.shy);
+    const uint32_t cxA = cc(2 * p.kx + p.parA, a.ncx, a.dLx, a.shx);
+    const uint32_t cxB = cc(2 * p.kx + p.parB, a.ncx, a.dLx, a.shx);
+    const int base = a.cell0 + p.inst * a.cstride;
+    cA = base + int((cz * a.ncy + cyA) * a.ncx + cxA);
+    cB = base + int((cz * a.ncy + cyB) * a.ncx + cxB);
+}
+
 // Update the pair from its neighbour sums and own words and store it at pair
 // q of the own colour's planes.
-template <bool AXZ>
+template <bool AXZ, int CM = kCellAny>
 __device__ __forceinline__ void pair_finish(const PairArgs &a, const PairSite &p, int colour, int hsel, bool h2, f2 g1,
                                             f2 g2, f2 g3, f2 htx, f2 hty, f2 htz, f2 h1x, f2 h1y, f2 h1z,
                                             ulonglong2 olo, ulonglong2 ohi, ulonglong2 *Wlo, ulonglong2 *Whi,
@@ -320,25 +355,7 @@ __device__ __forceinline__ void pair_finish(const PairArgs &a, const PairSite &p
         f2_split(w, wA, wB);
         const int tA = wA != 0.0f ? 1 : 0, tB = wB != 0.0f ? 1 : 0;
         int cA, cB;
-        if (a.cell_formula) {
-            auto cc = [](uint32_t v, uint32_t n, const FastDiv &d, int sh) {
-                return sh >= 0 ? v >> sh : fast_div(v * n, d);
-            };
-            const uint32_t cz = cc(p.z, a.ncz, a.dLz, a.shz);
-            const uint32_t cyA = cc(p.y2, a.ncy, a.dLy, a.shy), cyB = cc(p.y2 + a.Ly2, a.ncy, a.dLy, a.shy);
-            const uint32_t cxA = cc(2 * p.kx + p.parA, a.ncx, a.dLx, a.shx);
-            const uint32_t cxB = cc(2 * p.kx + p.parB, a.ncx, a.dLx, a.shx);
-            const int base = a.cell0 + p.inst * a.cstride;
-            cA = base + int((cz * a.ncy + cyA) * a.ncx + cxA);
-            cB = base + int((cz * a.ncy + cyB) * a.ncx + cxB);
-        } else {
-            // general slots of the two sites within the instance
-            const uint32_t slotA = uint32_t(colour) * a.nhalf + (p.z * a.Ly + p.y2) * a.hx + p.kx;
-            const uint32_t slotB = slotA + a.Ly2 * a.hx;
-            const int *cell = a.cell + int64_t(p.inst) * a.n_inst_sites;
-            cA = cell[slotA];
-            cB = cell[slotB];
-        }
+        pair_cells<CM>(a, p, colour, cA, cB);
         sig = f2_make(a.sigma[(cA * TTS_MAX_SPECIES + tA) * 2 + hsel], a.sigma[(cB * TTS_MAX_SPECIES + tB) * 2 + hsel]);
     }
     pair_update<AXZ>(sx, sy, sz, htx, hty, htz, h1x, h1y, h1z, w, a.noise != 0, sig, g1, g2, g3, a.k, h2);
@@ -357,11 +374,11 @@ __device__ __forceinline__ void pair_finish(const PairArgs &a, const PairSite &p
 // flight measured slower.
 // One block's worth of pairs: block index bx of a row of blocks (BX pairs x
 // BY pair rows), plane z, instance inst.
-template <bool AXZ>
+template <bool AXZ, int CM>
 __device__ __forceinline__ void pair_block(const PairArgs &a, int colour, int hsel, bool h2, int pass, uint32_t bx,
                                            uint32_t z, int inst)
 {
-    const uint32_t yb = bx / a.nkx;
+    const uint32_t yb = fast_div(bx, a.dnkx);
     const uint32_t kx = (bx - yb * a.nkx) * blockDim.x + threadIdx.x;
     const uint32_t y2 = yb * blockDim.y + threadIdx.y;
     const uint32_t hx = a.hx, Ly2 = a.Ly2, Lz = a.Lz;
@@ -397,18 +414,19 @@ __device__ __forceinline__ void pair_block(const PairArgs &a, int colour, int hs
     neighbour_sums(p, hx, Ly2, Olo, Ohi, Olo, Ohi, Olo, Ohi, (zp * Ly2 + y2) * hx, (zm * Ly2 + y2) * hx, r0,
                    (z * Ly2 + yp) * hx, (z * Ly2 + ym) * hx, htx, hty, htz, h1x, h1y, h1z);
     const uint32_t q = r0 + kx;
-    pair_finish<AXZ>(a, p, colour, hsel, h2, g1, g2, g3, htx, hty, htz, h1x, h1y, h1z, Wlo[q], Whi[q], Wlo, Whi, q);
+    pair_finish<AXZ, CM>(a, p, colour, hsel, h2, g1, g2, g3, htx, hty, htz, h1x, h1y, h1z, Wlo[q], Whi[q], Wlo, Whi,
+                         q);
 }
 
 // SW: the launch is a leading or trailing pass of the merged sweep (compiled
 // apart so that the other passes carry none of its code).  Those run on a
 // persistent grid that walks the (row block, z, instance) blocks, so that a
 // trailing pass the sweep skips costs one early exit per resident CTA.
-template <bool AXZ, bool SW>
+template <bool AXZ, bool SW, int CM>
 __global__ void __launch_bounds__(256, 4) checker_pair_kernel(PairArgs a, int colour, int hsel, int pass)
 {
     if (!SW) {
-        pair_block<AXZ>(a, colour, hsel, false, pass, blockIdx.x, blockIdx.y, blockIdx.z);
+        pair_block<AXZ, CM>(a, colour, hsel, false, pass, blockIdx.x, blockIdx.y, blockIdx.z);
         return;
     }
     int hd = -1;
@@ -420,7 +438,7 @@ __global__ void __launch_bounds__(256, 4) checker_pair_kernel(PairArgs a, int co
     for (uint64_t v = blockIdx.x; v < nvb; v += gridDim.x) {
         const uint32_t bx = static_cast<uint32_t>(v % nbx);
         const uint64_t r = v / nbx;
-        pair_block<AXZ>(a, colour, hsel, h2, pass, bx, static_cast<uint32_t>(r % a.Lz), static_cast<int>(r / a.Lz));
+        pair_block<AXZ, CM>(a, colour, hsel, h2, pass, bx, static_cast<uint32_t>(r % a.Lz), static_cast<int>(r / a.Lz));
     }
 }
 
@@ -2207,6 +2225,28 @@ void row_block(const EngineState *e, int &bx, int &by)
     }
 }
 
+// The cell mode of the pair kernels for these arguments.
+int pair_cell_mode(const PairArgs &a)
+{
+    if (!a.cell_formula) return kCellMap;
+    return a.shx >= 0 && a.shy >= 0 && a.shz >= 0 ? kCellShift : kCellDiv;
+}
+
+using PairKernelFn = void (*)(PairArgs, int, int, int);
+
+template <bool AXZ, bool SW>
+PairKernelFn pair_kernel_fn_cm(int cm)
+{
+    return cm == kCellShift ? checker_pair_kernel<AXZ, SW, kCellShift>
+                            : (cm == kCellDiv ? checker_pair_kernel<AXZ, SW, kCellDiv> : checker_pair_kernel<AXZ, SW, kCellMap>);
+}
+
+PairKernelFn pair_kernel_fn(bool axz, bool sw, int cm)
+{
+    return axz ? (sw ? pair_kernel_fn_cm<true, true>(cm) : pair_kernel_fn_cm<true, false>(cm))
+               : (sw ? pair_kernel_fn_cm<false, true>(cm) : pair_kernel_fn_cm<false, false>(cm));
+}
+
 // Launch arguments of the FP32 pair kernels for a pass with step h(hsel).
 PairArgs pair_args(const EngineState *e, const StepParams &p, const DevBuffers &b, int hsel)
 {
@@ -2229,6 +2269,7 @@ PairArgs pair_args(const EngineState *e, const StepParams &p, const DevBuffers &
         int bx, by;
         row_block(e, bx, by);
         a.nkx = bx ? (a.hx + bx - 1) / bx : 0;
+        a.dnkx = make_fastdiv(std::max<uint32_t>(a.nkx, 1));
     }
     a.nhalf = static_cast<uint32_t>(e->n_total / e->n_inst / 2);
     a.npair = a.nhalf / 2;
@@ -2389,8 +2430,7 @@ cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuf
                 fn<<<e->tile_grid, 256, e->tile_smem, st>>>(a, e->tile, c, hsel, pass);
             } else {
                 const dim3 pgrid(a.nkx * ((a.Ly2 + rby - 1) / rby), e->shape[2], e->n_inst);
-                auto fn = e->axis_z ? (sw ? checker_pair_kernel<true, true> : checker_pair_kernel<true, false>)
-                                    : (sw ? checker_pair_kernel<false, true> : checker_pair_kernel<false, false>);
+                auto fn = pair_kernel_fn(e->axis_z, sw, pair_cell_mode(a));
                 if (sw) {
                     // one block per (row block, z, instance) for the leading pass; the
                     // trailing pass, often skipped, on a persistent grid of 8 CTAs a SM
