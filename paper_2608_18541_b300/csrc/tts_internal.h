@@ -61,6 +61,7 @@ struct DevInstance {
     double sigma_t, t0;                 // s
     double prof_peak, prof_t1, prof_t2; // step profile: peak T_e (K), end of stage 1, end of stage 2 (s)
     double dx[3];                       // m
+    double inv_dx2[3];                  // 1 / dx^2, m^-2
     double cell_volume;                 // m^3
     int obs_block_begin;                // first observable partial block
     int obs_block_count;
@@ -79,6 +80,7 @@ struct SpeciesParams {
     double inv_mu;    // T/J
     double kappa;     // 2K/mu, tesla
     double alpha;
+    double sig_c[2];  // thermal-field scale sqrt(2 alpha k_B / (gamma mu h)), h = dt/2, dt (T in K)
     double gprime;    // gamma / (1 + alpha^2)
     double K;         // J
 };
@@ -86,6 +88,7 @@ struct SpeciesParams {
 struct TtmParams {
     int active;
     double gamma_e, C_l, G, kappa_e, T0;
+    double inv_gamma_e, inv_C_l;
     int source, spatial;
     double sigma_xy, depth_z;   // angstrom
 };

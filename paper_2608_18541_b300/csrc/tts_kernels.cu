@@ -106,13 +106,12 @@ __device__ __forceinline__ void exact_flow(R &sx, R &sy, R &sz, R Bx, R By, R Bz
 template <typename R>
 __device__ __forceinline__ void write_sigma(const StepParams &p, double T, R *__restrict__ sigma, int64_t g)
 {
+    // sigma = sqrt(2 alpha k_B T / (gamma mu h)) (paper Eq. 2) as sqrt(T) times
+    // the per-species, per-h factor
+    const double rT = T > 0.0 ? sqrt(T) : 0.0;
     for (int t = 0; t < TTS_MAX_SPECIES; ++t)
         for (int hs = 0; hs < 2; ++hs) {
-            double v = 0.0;
-            if (t < p.nspecies && T > 0.0 && p.sp[t].alpha > 0.0) {
-                const double h = hs ? p.dt : 0.5 * p.dt;
-                v = sqrt(2.0 * p.sp[t].alpha * kBoltzmann * T / (kGyro * p.sp[t].mu * h));
-            }
+            const double v = t < p.nspecies ? p.sp[t].sig_c[hs] * rT : 0.0;
             sigma[(g * TTS_MAX_SPECIES + t) * 2 + hs] = static_cast<R>(v);
         }
 }
@@ -292,14 +291,14 @@ __global__ void ttm_increment_kernel(StepParams p, DevBuffers b, TtmParams tp, c
     const double Tc = Te[c];
     double lap = 0.0;
     if (nxc > 1)
-        lap += (Te[cz * nyc * nxc + cy * nxc + (cx + 1) % nxc] - 2.0 * Tc + Te[cz * nyc * nxc + cy * nxc + (cx + nxc - 1) % nxc]) /
-               (I.dx[0] * I.dx[0]);
+        lap += (Te[cz * nyc * nxc + cy * nxc + (cx + 1) % nxc] - 2.0 * Tc + Te[cz * nyc * nxc + cy * nxc + (cx + nxc - 1) % nxc]) *
+               I.inv_dx2[0];
     if (nyc > 1)
-        lap += (Te[cz * nyc * nxc + ((cy + 1) % nyc) * nxc + cx] - 2.0 * Tc + Te[cz * nyc * nxc + ((cy + nyc - 1) % nyc) * nxc + cx]) /
-               (I.dx[1] * I.dx[1]);
+        lap += (Te[cz * nyc * nxc + ((cy + 1) % nyc) * nxc + cx] - 2.0 * Tc + Te[cz * nyc * nxc + ((cy + nyc - 1) % nyc) * nxc + cx]) *
+               I.inv_dx2[1];
     if (nzc > 1)
         lap += (Te[((cz + 1) % nzc) * nyc * nxc + cy * nxc + cx] - 2.0 * Tc +
-                Te[((cz + nzc - 1) % nzc) * nyc * nxc + cy * nxc + cx]) / (I.dx[2] * I.dx[2]);
+                Te[((cz + nzc - 1) % nzc) * nyc * nxc + cy * nxc + cx]) * I.inv_dx2[2];
     double pulse = 0.0;
     if (tp.source != TTS_SOURCE_NONE) {
         const double z = (double(*b.step) * p.dt - I.t0) / I.sigma_t;
@@ -308,7 +307,7 @@ __global__ void ttm_increment_kernel(StepParams p, DevBuffers b, TtmParams tp, c
     const double src = pulse * b.src_shape[g];
     const double x = tp.G * (Tc - b.Tl[g]);
     b.ttm_scratch[g] = p.dt * (tp.kappa_e * lap - x + src);
-    b.Tl[g] += p.dt * x / tp.C_l;
+    b.Tl[g] += p.dt * x * tp.inv_C_l;
 }
 
 // New T_e of every cell and, from it, the noise table of the next step; the
@@ -319,7 +318,9 @@ __global__ void ttm_apply_kernel(StepParams p, DevBuffers b, TtmParams tp, int n
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (inc_step && g == 0) *b.step += 1;
     if (g >= ncells_total) return;
-    const double T = sqrt(2.0 * (0.5 * tp.gamma_e * b.Te[g] * b.Te[g] + b.ttm_scratch[g]) / tp.gamma_e);
+    // electron energy gamma_e T^2 / 2 plus the increment, back to T
+    const double T0 = b.Te[g];
+    const double T = sqrt(fma(2.0 * b.ttm_scratch[g], tp.inv_gamma_e, T0 * T0));
     b.Te[g] = T;
     write_sigma<R>(p, T, static_cast<R *>(b.sigma), g);
 }

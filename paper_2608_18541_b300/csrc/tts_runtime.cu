@@ -594,6 +594,12 @@ int tts_create_system(const tts_system_desc *desc, void *stream, tts_system **ou
         p.B[k] = desc->B[k];
     }
     p.dt = desc->dt;
+    for (int t = 0; t < desc->nspecies; ++t)
+        for (int hs = 0; hs < 2; ++hs) {
+            const SpeciesParams &sp = p.sp[t];
+            const double h = hs ? p.dt : 0.5 * p.dt;
+            p.sp[t].sig_c[hs] = sp.alpha > 0.0 ? std::sqrt(2.0 * sp.alpha * kBoltzmann / (kGyro * sp.mu * h)) : 0.0;
+        }
     p.key0 = static_cast<uint32_t>(desc->seed & 0xffffffffu);
     p.key1 = static_cast<uint32_t>(desc->seed >> 32);
     p.nspecies = desc->nspecies;
@@ -758,6 +764,7 @@ int tts_set_ttm_grid(tts_system *s, const tts_ttm_desc *t)
         for (int k = 0; k < 3; ++k) {
             di.cells[k] = t->cells[k];
             di.dx[k] = h.dx[k];
+            di.inv_dx2[k] = 1.0 / (h.dx[k] * h.dx[k]);
         }
         di.cell_volume = h.vol;
         di.substeps = profile ? 1 : h.substeps;
@@ -780,6 +787,8 @@ int tts_set_ttm_grid(tts_system *s, const tts_ttm_desc *t)
     tp.active = 1;
     tp.gamma_e = t->gamma_e;
     tp.C_l = t->C_l;
+    tp.inv_gamma_e = 1.0 / t->gamma_e;
+    tp.inv_C_l = 1.0 / t->C_l;
     tp.G = t->G;
     tp.kappa_e = t->kappa_e;
     tp.T0 = t->T0;
