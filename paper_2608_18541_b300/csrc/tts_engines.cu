@@ -1021,25 +1021,69 @@ __device__ __forceinline__ double obs_scale(const PairObsArgs &o, int f)
 
 constexpr int kObsTerms = 8;
 
-// Sum NF doubles over the kObsBlock threads: shared memory, then warp w sums
-// the fields f = w, w + 4, ... (each lane four threads' values, then a
-// five-level shuffle tree): a fixed order, about a fifth of the FP64 adds of
-// a shuffle tree over every field in every lane.
-// The sum of field f is multiplied by scale(f) and stored at out[f].
+// Compensated sums.  A pair (s, c) of floats stands for s + c; adding x
+// replaces s by the rounded s + x and adds that addition's rounding error,
+// computed exactly by TwoSum (Knuth, TAOCP vol. 2, Sec. 4.2.2), to c.  Only
+// the additions into c round, each by at most eps = 2^-24 times the c it
+// makes, and a c that is d additions deep holds at most d eps times the sum
+// of the |terms| below it.  A block partial is d <= 12 deep on every path
+// (four pairs a lane, the two lanes, four threads, five shuffle levels), so
+// it is within 144 eps^2 sum|x| < 2^-40 sum|x| of the exact sum of its 1024
+// FP32 site terms (FP64 accumulation in the same order would guarantee
+// 12 * 2^-53 sum|x|), far below the terms' own FP32 rounding (up to
+// eps sum|x|).  Block partials are summed in FP64.
+struct Comp2 {                 // both lanes of an f2
+    f2 s, c;
+};
+__device__ __forceinline__ void comp_add(Comp2 &a, f2 x)
+{
+    const f2 t = a.s + x;
+    const f2 xv = t - a.s;                 // the part of x that reached t
+    const f2 e = (a.s - (t - xv)) + (x - xv);
+    a.s = t;
+    a.c = a.c + e;
+}
+struct Comp1 {
+    float s, c;
+};
+__device__ __forceinline__ Comp1 comp_sum(Comp1 a, Comp1 b)
+{
+    const float t = __fadd_rn(a.s, b.s);
+    const float bv = __fsub_rn(t, a.s);
+    const float e = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bv)), __fsub_rn(b.s, bv));
+    return Comp1{t, __fadd_rn(__fadd_rn(a.c, b.c), e)};
+}
+__device__ __forceinline__ Comp1 comp_lanes(const Comp2 &a)
+{
+    float sA, sB, cA, cB;
+    f2_split(a.s, sA, sB);
+    f2_split(a.c, cA, cB);
+    return comp_sum(Comp1{sA, cA}, Comp1{sB, cB});
+}
+
+// Sum NF compensated values over the kObsBlock threads: shared memory, then
+// warp w sums the fields f = w, w + 4, ... (each lane four threads' values,
+// then a five-level shuffle tree), in a fixed order.  Field f's sum, as a
+// double, times scale(f) is stored at out[f].
 template <int NF, typename Scale>
-__device__ __forceinline__ void block_sum_fields(const double (&v)[NF], Scale scale, double *out)
+__device__ __forceinline__ void block_sum_comp(const Comp1 (&v)[NF], Scale scale, double *out)
 {
     static_assert(kObsBlock == 128, "four warps of 32");
-    __shared__ double sh[NF][kObsBlock];
+    __shared__ float shs[NF][kObsBlock], shc[NF][kObsBlock];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) sh[f][threadIdx.x] = v[f];
+    for (int f = 0; f < NF; ++f) {
+        shs[f][threadIdx.x] = v[f].s;
+        shc[f][threadIdx.x] = v[f].c;
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int f = warp; f < NF; f += kObsBlock / 32) {
-        double x = (sh[f][lane] + sh[f][lane + 32]) + (sh[f][lane + 64] + sh[f][lane + 96]);
+        auto at = [&](int i) { return Comp1{shs[f][i], shc[f][i]}; };
+        Comp1 x = comp_sum(comp_sum(at(lane), at(lane + 32)), comp_sum(at(lane + 64), at(lane + 96)));
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) out[f] = x * scale(f);
+        for (int o = 16; o > 0; o >>= 1)
+            x = comp_sum(x, Comp1{__shfl_down_sync(0xffffffffu, x.s, o), __shfl_down_sync(0xffffffffu, x.c, o)});
+        if (lane == 0) out[f] = (double(x.s) + double(x.c)) * scale(f);
     }
     __syncthreads();
 }
@@ -1053,9 +1097,9 @@ __global__ void __launch_bounds__(kObsBlock) checker_pair_obs_kernel(PairArgs a,
     for (int blk = blockIdx.x; blk < o.obs_blocks; blk += gridDim.x) {
         const int inst = o.obs_block_inst[blk];
         const uint32_t local = static_cast<uint32_t>(blk - o.inst[inst].obs_block_begin);
-        double all[kObsTerms], one[kObsTerms];
+        Comp2 all[kObsTerms], one[kObsTerms];
 #pragma unroll
-        for (int t = 0; t < kObsTerms; ++t) all[t] = one[t] = 0.0;
+        for (int t = 0; t < kObsTerms; ++t) all[t] = one[t] = Comp2{f2{0}, f2{0}};
         int n_all = 0, n_one = 0;
         const ulonglong2 *base = pair_state(a) + int64_t(inst) * a.n_inst_sites;
         for (int j = 0; j < kObsSpan / 2 / kObsBlock; ++j) {
@@ -1091,35 +1135,30 @@ __global__ void __launch_bounds__(kObsBlock) checker_pair_obs_kernel(PairArgs a,
                                         fma2(sz, Bz, fma2(sy, By, sx * Bx))};
             float wA, wB;
             f2_split(w, wA, wB);
-            const double dwA = wA, dwB = wB;
             n_all += 2;
             n_one += (wA != 0.0f) + (wB != 0.0f);
 #pragma unroll
             for (int t = 0; t < kObsTerms; ++t) {
-                float vA, vB;
-                f2_split(term[t], vA, vB);
-                const double dA = vA, dB = vB;
-                all[t] += dA;
-                all[t] += dB;
-                one[t] = fma(dwA, dA, one[t]);
-                one[t] = fma(dwB, dB, one[t]);
+                comp_add(all[t], term[t]);
+                comp_add(one[t], w * term[t]);        // exact: w is 0 or 1
             }
         }
-        double acc[kObsFields];
+        Comp1 acc[kObsFields];
 #pragma unroll
-        for (int f = 0; f < kObsFields; ++f) acc[f] = 0.0;
-        acc[0] = double(n_all - n_one);
-        acc[12] = double(n_one);
+        for (int f = 0; f < kObsFields; ++f) acc[f] = Comp1{0.0f, 0.0f};
+        acc[0] = Comp1{float(n_all - n_one), 0.0f};   // counts below 2^24: exact
+        acc[12] = Comp1{float(n_one), 0.0f};
 #pragma unroll
         for (int t = 0; t < kObsTerms; ++t) {
             // species 0: all sites minus species 1, term by term
-            const double v0 = all[t] - one[t], v1 = one[t];
+            const Comp1 v1 = comp_lanes(one[t]);
+            const Comp1 v0 = comp_sum(comp_lanes(all[t]), Comp1{-v1.s, -v1.c});
             const int f = t < 3 ? 1 + t : 4 + t;       // s -> 1..3; the five others -> 7..11
             acc[f] = v0;
             acc[12 + f] = v1;
         }
-        block_sum_fields<kObsFields>(acc, [&](int f) { return obs_scale(o, f); },
-                                     o.obs_partial + int64_t(blk) * kObsFields);
+        block_sum_comp<kObsFields>(acc, [&](int f) { return obs_scale(o, f); },
+                                   o.obs_partial + int64_t(blk) * kObsFields);
     }
 }
 

@@ -242,9 +242,10 @@ __device__ __forceinline__ void pair_update(f2 &sx, f2 &sy, f2 &sz, f2 htx, f2 h
     const f2 iD = f2_map<rcp_approx>(opc + omcE);
     const f2 cp = (opc - omcE) * iD;
     const f2 rho = (em + em) * iD;
-    // sin / cos of phi: Taylor through phi^5 / phi^6 below 1/16 rad (the
-    // truncation, below phi^7 / 5040, is under 1e-11 relative); the usual
-    // sub-step angle is ~0.01 rad
+    // sin / cos of phi: Taylor through phi^5 / phi^6 below 1/4 rad (the
+    // truncation, below phi^7 / 7! = 1.2e-8 there, is under one FP32 ulp of
+    // sin phi).  Thermal fields of a few thousand kelvin give sub-step angles
+    // of 0.02 to 0.2 rad.
     const f2 p2 = phi * phi;
     f2 sn = phi * fma2(p2, fma2(p2, k.s5, k.s3), k.one);
     f2 cs = fma2(p2, fma2(p2, fma2(p2, k.c6, k.c4), k.c2), k.one);
@@ -252,13 +253,13 @@ __device__ __forceinline__ void pair_update(f2 &sx, f2 &sy, f2 &sz, f2 htx, f2 h
     f2_split(phi, phA, phB);
     f2_split(B2, b2A, b2B);
     // one rarely taken branch for a large angle or a vanishing field in either lane
-    const bool slow = !(phA < 0.0625f && phB < 0.0625f && b2A > 1e-30f && b2B > 1e-30f);
+    const bool slow = !(phA < 0.25f && phB < 0.25f && b2A > 1e-30f && b2B > 1e-30f);
     if (slow) {
         float snA, snB, csA, csB;
         f2_split(sn, snA, snB);
         f2_split(cs, csA, csB);
-        if (!(phA < 0.0625f)) sincosf(phA, &snA, &csA);
-        if (!(phB < 0.0625f)) sincosf(phB, &snB, &csB);
+        if (!(phA < 0.25f)) sincosf(phA, &snA, &csA);
+        if (!(phB < 0.25f)) sincosf(phB, &snB, &csB);
         sn = f2_make(snA, snB);
         cs = f2_make(csA, csB);
     }

@@ -1,8 +1,10 @@
 """Every observable field of the FP32 engines against the FP64 oracle.
 
 The FP32 checker and resident engines compute each site's observable terms
-from FP32 spins and sum them in FP64 (the per-sublattice magnetisation and
-energy reductions).  Each field is compared with the oracle's within a bound
+from FP32 spins.  The resident engine sums them in FP64; the checker engine
+sums a block's 1024 terms with compensated (TwoSum) FP32 additions, within
+2^-40 of the sum of their magnitudes, and the block partials in FP64 (the
+per-sublattice magnetisation and energy reductions).  Each field is compared with the oracle's within a bound
 propagated from a bound eps on every spin component's error: the rounding of
 a given state to FP32 (first test), or the 2e-5 FP32 parity bar after up to
 200 steps (second test).  The bounds are worst-case sums over sites, computed
