@@ -113,9 +113,9 @@ def _peaks():
         return 6400.0, "fallback"
 
 
-def _traffic(kernel, precision):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, or None when it does not match the current kernel source."""
+def _record(kernel, precision):
+    """The committed ncu record of the dominant kernel (profiles/traffic.json),
+    or None when it does not match the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -133,7 +133,32 @@ def _traffic(kernel, precision):
                 h.update(f.read())
     except (OSError, KeyError):
         return None
-    return e["bytes_per_launch"] if h.hexdigest()[:16] == e.get("sources_sha") else None
+    return e if h.hexdigest()[:16] == e.get("sources_sha") else None
+
+
+def _traffic(kernel, precision):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    record, or None when it does not match the current kernel sources."""
+    e = _record(kernel, precision)
+    return e["bytes_per_launch"] if e else None
+
+
+def _issue(kernel, precision, avg_launch_ms, clocks):
+    """Instruction-issue roofline of the dominant kernel: its warp instructions
+    per launch (committed ncu record) over the live launch time, against
+    4 schedulers x SMs x the SM clock measured during the timed region."""
+    e = _record(kernel, precision)
+    if not e or not e.get("warp_inst_per_launch") or not avg_launch_ms:
+        return None
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = clocks["sm_mhz"] if clocks and clocks.get("sm_mhz") else None
+    if not mhz:
+        return None
+    achieved = e["warp_inst_per_launch"] / (avg_launch_ms / 1e3)
+    peak = 4.0 * sms * mhz * 1e6
+    return {"achieved": achieved, "peak": peak, "unit": "warp instructions/s", "frac": achieved / peak,
+            "warp_inst_per_launch": e["warp_inst_per_launch"], "sm_mhz": mhz, "sms": sms}
 
 
 def ensemble_leg(P, W, stream, steps=200, sample=64):
@@ -203,42 +228,61 @@ def merged_leg(P, sysd, ttm, args, stream, spins):
             "note": "sweep closed at every sampling step (once per chunk) and at the end of every call"}
 
 
+def _launches_per_dt(g, chunk):
+    a = g.info().kernel_launches
+    g.profile_enable(True)            # direct launches, so that every kernel is counted
+    g.step(chunk)
+    g.sync()
+    ms, steps, ss = g.profile_read()
+    g.profile_enable(False)
+    return (g.info().kernel_launches - a) / chunk, ms, steps, ss
+
+
 def fused_leg(P, g, args, stream, spins, peak, peak_kind):
     """The same system with the fused symmetric sweep (checker_sweep_kernel:
-    the three colour passes of a step in one launch, the last launch
-    configuration the FP32 checker engine offers): its whole-step rate, the
-    roofline of its launch, and the DRAM traffic of one launch when the ncu
+    the three colour passes of a step in one launch).  The FP32 checker engine
+    offers it last among its launch configurations, one per fusion depth (z
+    segments per instance), the cost model's choice last of all.  Every fused
+    configuration is timed; the fastest is reported with its whole-step rate,
+    the roofline of its launch, and the DRAM traffic of one launch when the ncu
     record matches the sources.  Bitwise the same spins as the headline's
     separate passes; reported beside it."""
     import torch
     cur, n = g.set_config(-1)
     if g.engine != "checker" or args.precision != 32 or n < 2:
         return None
-    g.set_config(n - 1)
-    # the fused configuration launches one spin kernel a step instead of three
-    a = g.info().kernel_launches
-    g.profile_enable(True)
-    g.step(args.chunk)
-    g.sync()
-    kms, ksteps, kss = g.profile_read()
-    g.profile_enable(False)
-    per_step = (g.info().kernel_launches - a) / args.chunk
+    # the fused configurations launch one spin kernel a step instead of three
+    fused = []
+    for k in range(n - 1, -1, -1):
+        g.set_config(k)
+        per, kms, ksteps, kss = _launches_per_dt(g, args.chunk)
+        if fused and per != fused[0][1]:
+            break
+        fused.append((k, per, kms, ksteps, kss))
     steps = max(1, min(args.steps, 5))
-    g.step(args.chunk)
-    g.sync()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
+    rates = {}
+    best = None
+    for k, per_step, kms, ksteps, kss in fused:
+        g.set_config(k)
         g.step(args.chunk)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+        g.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            g.step(args.chunk)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        rates[str(k)] = spins * steps * args.chunk / (ms / 1e3)
+        if best is None or ms < best[0]:
+            best = (ms, k, per_step, kms, ksteps, kss)
     g.set_config(cur)
+    ms, k, per_step, kms, ksteps, kss = best
     bpu = BYTES_PER_SPIN_STEP[args.precision]
     achieved = bpu * kss / (kms / 1e3) / 1e9
     return {"value": spins * steps * args.chunk / (ms / 1e3), "unit": "spin-steps/s", "ms_per_step": ms / steps,
-            "steps": steps, "kernels_per_dt": per_step, "config": n - 1,
+            "steps": steps, "kernels_per_dt": per_step, "config": k, "configs_timed": rates,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": _traffic("step_checker_sweep", args.precision),
                          "kernel": "checker_sweep_kernel", "bytes_per_unit": bpu, "units_per_launch": spins,
@@ -419,8 +463,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-single", action="store_true", help="skip the single-instance roofline legs")
     ap.add_argument("--no-fused", action="store_true", help="skip the fused-sweep leg")
-    ap.add_argument("--config", type=int, default=-1,
-                    help="launch configuration of the timed system (tts_set_config index; -1: the default)")
+    ap.add_argument("--config", default="-1",
+                    help="launch configuration of the timed system (tts_set_config index; -1: the default; "
+                         "'last': the last one offered, for the FP32 checker the fused sweep at the cost "
+                         "model's fusion depth)")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-merged", action="store_true")
     args = ap.parse_args()
@@ -454,8 +500,10 @@ def main():
     g = P.System(sysd, ttm, precision=args.precision, engine=args.engine, stream=stream.cuda_stream,
                  instance_base=rank * n_inst_local)
     spins = g.n_total
-    if args.config >= 0:
-        g.set_config(args.config)
+    if args.config == "last":
+        g.set_config(g.set_config(-1)[1] - 1)
+    elif int(args.config) >= 0:
+        g.set_config(int(args.config))
     initial = g.get_state()
     for _ in range(args.warmup):
         g.step(args.chunk)
@@ -548,6 +596,8 @@ def main():
                 "traffic": _traffic(kernel_name, args.precision), "kernel": kernel_name,
                 "bytes_per_unit": bpu, "units_per_launch": spins,
                 "avg_launch_ms": kern_ms / max(kern_steps, 1)}
+    # the kernel is bound by instruction issue: the same launch against that ceiling
+    roofline["issue"] = _issue(kernel_name, args.precision, roofline["avg_launch_ms"], clocks)
     engine = g.engine
     from paper_2608_18541_b300 import workloads as W
     merged = None

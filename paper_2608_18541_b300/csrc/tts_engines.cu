@@ -1064,11 +1064,13 @@ __device__ __forceinline__ Comp1 comp_lanes(const Comp2 &a)
 // Sum NF compensated values over the kObsBlock threads: shared memory, then
 // warp w sums the fields f = w, w + 4, ... (each lane four threads' values,
 // then a five-level shuffle tree), in a fixed order.  Field f's sum, as a
-// double, times scale(f) is stored at out[f].
+// double, times scale(f) is stored at out[f] by thread f (the FP64 work of
+// all fields in one warp instruction each: the FP64 pipe takes 16 clocks a
+// warp instruction however few lanes are active).
 template <int NF, typename Scale>
 __device__ __forceinline__ void block_sum_comp(const Comp1 (&v)[NF], Scale scale, double *out)
 {
-    static_assert(kObsBlock == 128, "four warps of 32");
+    static_assert(kObsBlock == 128 && NF <= 32, "four warps of 32, one lane a field");
     __shared__ float shs[NF][kObsBlock], shc[NF][kObsBlock];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -1083,8 +1085,14 @@ __device__ __forceinline__ void block_sum_comp(const Comp1 (&v)[NF], Scale scale
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
             x = comp_sum(x, Comp1{__shfl_down_sync(0xffffffffu, x.s, o), __shfl_down_sync(0xffffffffu, x.c, o)});
-        if (lane == 0) out[f] = (double(x.s) + double(x.c)) * scale(f);
+        __syncwarp();
+        if (lane == 0) {                // row f is read by this warp only, and no longer
+            shs[f][0] = x.s;
+            shc[f][0] = x.c;
+        }
     }
+    __syncthreads();
+    if (threadIdx.x < NF) out[threadIdx.x] = (double(shs[threadIdx.x][0]) + double(shc[threadIdx.x][0])) * scale(threadIdx.x);
     __syncthreads();
 }
 
@@ -2126,7 +2134,11 @@ int engine_create(const tts_system_desc &d, const std::vector<HostInstance> &hos
             cudaMemsetAsync(e->done, 0, sizeof(unsigned), st);
             // offered to the autotuner; the separate passes stay the default
             // (on 128^3 x 4 they measured about twice as fast: the fused
-            // launch is bound by the latency of one update a warp per step)
+            // launch is bound by the latency of one update a warp per step).
+            // Fusion depth: z segments per instance 1, 2, 4, 8 (each at least
+            // four planes long), then the cost model's choice, last.
+            for (uint32_t sg : {1u, 2u, 4u, 8u})
+                if (sg != e->sweep.nseg && sg <= e->shape[2] / 4) e->configs.push_back({-2, static_cast<int>(sg)});
             e->configs.push_back({-2, 0});
         } else {
             e->S1 = e->S;
@@ -2401,13 +2413,14 @@ cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuf
         // the three passes of the step in one launch (checker_sweep_kernel)
         PairArgs a = pair_args(e, p, b, 0);
         SweepArgs w{};
+        const uint32_t nseg = e->by > 0 ? static_cast<uint32_t>(e->by) : e->sweep.nseg;
         w.R = e->sweep.R;
-        w.nseg = e->sweep.nseg;
+        w.nseg = nseg;
         w.done = e->done;
-        w.ctas = e->sweep.C * e->sweep.nseg * static_cast<uint32_t>(e->n_inst);
+        w.ctas = e->sweep.C * nseg * static_cast<uint32_t>(e->n_inst);
         w.cur = e->cur;
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(e->sweep.C, e->sweep.nseg, e->n_inst);
+        cfg.gridDim = dim3(e->sweep.C, nseg, e->n_inst);
         cfg.blockDim = dim3(e->sweep.threads, 1, 1);
         cfg.dynamicSmemBytes = e->sweep.smem;
         cfg.stream = st;

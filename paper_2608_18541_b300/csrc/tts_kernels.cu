@@ -411,7 +411,9 @@ __global__ void __launch_bounds__(kObsBlock) obs_partial_kernel(StepParams p, De
 // 4..6 unused, 7 exchange energy (half of mu s.h per atom, each pair counted
 // twice), 8 anisotropy, 9 Zeeman, 10 sum |s x H|^2, 11 sum s.H.  The moment-
 // weighted direction is sum_t mu_t sum_{i in t} s_i / sum_t mu_t n_t.
-__global__ void obs_reduce_kernel(StepParams p, DevBuffers b, int mode)
+constexpr int kObsReduceThreads = 32 * (kObsFields + 4);   // one warp a field
+
+__global__ void __launch_bounds__(kObsReduceThreads) obs_reduce_kernel(StepParams p, DevBuffers b, int mode)
 {
     const int64_t step = *b.step;
     const int64_t clock = p.lattice_on ? *p.lstep : step;
@@ -419,34 +421,32 @@ __global__ void obs_reduce_kernel(StepParams p, DevBuffers b, int mode)
     if (!sample) return;
     const int inst = blockIdx.x;
     const DevInstance I = b.inst[inst];
-    // fixed order: thread j sums blocks j, j + blockDim, ... (and TTM cells,
-    // lattice partials likewise); then a tree.  Extra fields: sum T_e, sum
-    // T_l, kinetic and pair energy.
+    // warp f sums field f in a fixed order: lane j the blocks j, j + 32, ...
+    // (TTM cells and lattice partials likewise), then a shuffle tree.  Extra
+    // fields: sum T_e, sum T_l, kinetic and pair energy.  One warp a field
+    // spreads the FP64 adds over the SM's four schedulers.
     constexpr int NF = kObsFields + 4;
-    __shared__ double red[NF][128];
-    double part[NF];
-    for (int k = 0; k < NF; ++k) part[k] = 0.0;
-    for (int blk = I.obs_block_begin + threadIdx.x; blk < I.obs_block_begin + I.obs_block_count; blk += blockDim.x) {
-        for (int k = 0; k < kObsFields; ++k) part[k] += b.obs_partial[int64_t(blk) * kObsFields + k];
-        if (p.lattice_on && mode == 0) {
-            part[kObsFields + 2] += p.lat_partial[2 * int64_t(blk)];
-            part[kObsFields + 3] += p.lat_partial[2 * int64_t(blk) + 1];
-        }
+    __shared__ double red[NF];
+    const int lane = threadIdx.x & 31, f = threadIdx.x >> 5;
+    double part = 0.0;
+    const int blk_end = I.obs_block_begin + I.obs_block_count;
+    if (f < kObsFields) {
+        for (int blk = I.obs_block_begin + lane; blk < blk_end; blk += 32)
+            part += b.obs_partial[int64_t(blk) * kObsFields + f];
+    } else if (f < kObsFields + 2) {
+        const double *T = f == kObsFields ? b.Te : b.Tl;
+        for (int c = lane; c < I.ncells; c += 32) part += T[I.cell_begin + c];
+    } else if (f < NF && p.lattice_on && mode == 0) {
+        for (int blk = I.obs_block_begin + lane; blk < blk_end; blk += 32)
+            part += p.lat_partial[2 * int64_t(blk) + (f - kObsFields - 2)];
     }
-    for (int c = threadIdx.x; c < I.ncells; c += blockDim.x) {
-        part[kObsFields] += b.Te[I.cell_begin + c];
-        part[kObsFields + 1] += b.Tl[I.cell_begin + c];
-    }
-    for (int k = 0; k < NF; ++k) red[k][threadIdx.x] = part[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if (lane == 0 && f < NF) red[f] = part;
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int k = 0; k < NF; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
-        __syncthreads();
-    }
     if (threadIdx.x != 0) return;
     double tot[kObsFields];
-    for (int k = 0; k < kObsFields; ++k) tot[k] = red[k][0];
+    for (int k = 0; k < kObsFields; ++k) tot[k] = red[k];
     double rec[TTS_NOBS];
     for (int k = 0; k < TTS_NOBS; ++k) rec[k] = 0.0;
     // a moving lattice has advanced the spin-step counter already
@@ -474,10 +474,10 @@ __global__ void obs_reduce_kernel(StepParams p, DevBuffers b, int mode)
     rec[7] = mux / musum;
     rec[8] = muy / musum;
     rec[9] = muz / musum;
-    rec[15] = red[kObsFields][0] / I.ncells;
-    rec[16] = red[kObsFields + 1][0] / I.ncells;
+    rec[15] = red[kObsFields] / I.ncells;
+    rec[16] = red[kObsFields + 1] / I.ncells;
     if (p.lattice_on && mode == 0) {
-        const double ek = red[kObsFields + 2][0], em = red[kObsFields + 3][0];
+        const double ek = red[kObsFields + 2], em = red[kObsFields + 3];
         rec[16] = 2.0 * ek / (3.0 * double(I.n) * kBoltzmann);
         rec[17] = ek;
         rec[18] = em;
@@ -663,7 +663,7 @@ cudaError_t launch_obs(StepParams p, const DevBuffers &b, int precision, int nbl
 
 cudaError_t launch_obs_reduce(const StepParams &p, const DevBuffers &b, int mode, cudaStream_t st)
 {
-    obs_reduce_kernel<<<p.n_instances, 128, 0, st>>>(p, b, mode);
+    obs_reduce_kernel<<<p.n_instances, kObsReduceThreads, 0, st>>>(p, b, mode);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || mode != 0 || p.lattice_on) return e;
     step_inc_kernel<<<1, 1, 0, st>>>(b.step);

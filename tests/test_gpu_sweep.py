@@ -2,8 +2,9 @@
 the three colour passes of a step in one launch, a wavefront along z with
 the planes in flight in shared memory.  Every site sees the same inputs,
 noise and arithmetic as in the three separate passes, so the spins must be
-bitwise those of the separate-pass kernel, for any segmentation, cluster
-shape, instance count, call length and checkpoint in between; and within the
+bitwise those of the separate-pass kernel, for every fusion depth (z segments
+per instance) offered, cluster shape, instance count, call length and
+checkpoint in between; and within the
 2e-5 FP32 bar of the FP64 oracle over 200 steps."""
 import numpy as np
 import pytest
@@ -28,16 +29,22 @@ def _launches_per_step(g, n=4):
 
 
 def _fused_and_separate(g):
-    """The fused sweep (the last configuration offered: one spin kernel a
-    step) and the default separate-pass configuration."""
+    """The fused sweep configurations (the last ones offered, one per fusion
+    depth: one spin kernel a step) and the default separate-pass
+    configuration."""
     cur, n = g.set_config(-1)
     assert cur == 0 and n >= 2
-    g.set_config(n - 1)
-    k0 = _launches_per_step(g)
     g.set_config(0)
     k1 = _launches_per_step(g)
-    assert k1 - k0 == 2, (k0, k1)     # three pass launches replaced by one
-    return n - 1, 0
+    fused = []
+    for c in range(n - 1, 0, -1):
+        g.set_config(c)
+        k0 = _launches_per_step(g)
+        if k1 - k0 != 2:              # three pass launches replaced by one
+            break
+        fused.append(c)
+    assert fused and fused[0] == n - 1
+    return fused, 0
 
 
 @pytest.mark.parametrize("shape,ninst,ttm", [
@@ -54,10 +61,11 @@ def test_fused_sweep_is_bitwise_the_separate_passes(shape, ninst, ttm):
     g = P.System(sysd, t, precision=32, engine="checker")
     assert g.engine == "checker"
     fused, sep = _fused_and_separate(g)
+    assert len(fused) >= 2            # fusion depths: z segments per instance
     g.set_step(0)
     start = g.get_state()
     runs = {}
-    for c in (fused, sep):
+    for c in fused + [sep]:
         g.set_state(start)
         g.set_config(c)
         g.step(13)                    # odd: the state ends in the second buffer
@@ -66,10 +74,11 @@ def test_fused_sweep_is_bitwise_the_separate_passes(shape, ninst, ttm):
         g.set_state(mid)              # resume from a checkpoint taken mid-way
         g.step(20)
         runs[c] = ([g.get_spins(i) for i in range(ninst)], g.observables(0), g.get_ttm(0)[0])
-    for i in range(ninst):
-        assert np.array_equal(runs[fused][0][i], runs[sep][0][i]), i
-    assert np.array_equal(runs[fused][1], runs[sep][1])
-    assert np.array_equal(runs[fused][2], runs[sep][2])
+    for c in fused:
+        for i in range(ninst):
+            assert np.array_equal(runs[c][0][i], runs[sep][0][i]), (c, i)
+        assert np.array_equal(runs[c][1], runs[sep][1]), c
+        assert np.array_equal(runs[c][2], runs[sep][2]), c
 
 
 def test_fused_sweep_matches_oracle_200_steps():
@@ -94,7 +103,7 @@ def test_fused_sweep_full_size_instance_against_separate_passes():
     g.set_step(0)
     start = g.get_state()
     out = []
-    for c in (fused, sep):
+    for c in [fused[0], sep]:
         g.set_state(start)
         g.set_config(c)
         g.step(5)
