@@ -82,7 +82,7 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
 __device__ __forceinline__ float rsqrt_approx(float x)
 {
     float r;
-    asm("rsqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 __device__ __forceinline__ float rcp_approx(float x)
