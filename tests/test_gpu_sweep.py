@@ -31,19 +31,21 @@ def _launches_per_step(g, n=4):
 def _fused_and_separate(g):
     """The fused sweep configurations (the last ones offered, one per fusion
     depth: one spin kernel a step) and the default separate-pass
-    configuration."""
+    configuration (three pass launches a step per instance chain)."""
     cur, n = g.set_config(-1)
     assert cur == 0 and n >= 2
+    k = []
+    for c in range(n):
+        g.set_config(c)
+        k.append(_launches_per_step(g))
     g.set_config(0)
-    k1 = _launches_per_step(g)
     fused = []
     for c in range(n - 1, 0, -1):
-        g.set_config(c)
-        k0 = _launches_per_step(g)
-        if k1 - k0 != 2:              # three pass launches replaced by one
+        if k[c] != min(k):            # one spin kernel a step: the fewest launches
             break
         fused.append(c)
     assert fused and fused[0] == n - 1
+    assert k[0] - min(k) >= 2
     return fused, 0
 
 
