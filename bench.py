@@ -41,6 +41,9 @@ def _workload(name):
     if name == "gdfeco_128x4":
         sysd, ttm = W.config_gdfeco_large(128, 4)
         return sysd, ttm, "GdFeCo sc 128^3 x 4 realisations, 16^3 TTM grid, Gaussian spot 40 A, peak 2000 K"
+    if name == "gdfeco_128x1":
+        sysd, ttm = W.config_gdfeco_large(128, 1)
+        return sysd, ttm, "GdFeCo sc 128^3 x 1 realisation, 16^3 TTM grid, Gaussian spot 40 A, peak 2000 K"
     if name == "gdfeco_256x1":
         sysd, ttm = W.config_gdfeco_large(256, 1)
         return sysd, ttm, "GdFeCo sc 256^3 x 1 realisation, 16^3 TTM grid, Gaussian spot 40 A, peak 2000 K"

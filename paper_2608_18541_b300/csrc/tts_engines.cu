@@ -2433,7 +2433,7 @@ cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuf
         err = launch_sigma(p, b, p.ncells_total, e->precision, st);
         ++*kernels;
     }
-    if (err == cudaSuccess && ev0) err = cudaEventRecord(ev0, st);
+    if (err == cudaSuccess && ev0) err = cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal);
     const int npass = 2 * e->K - 1;
     // merged sweep: the first pass leads (dt/2 or a dt bridge), the last trails
     auto ctl = [&](int pass) {
@@ -2560,7 +2560,7 @@ cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuf
         err = cudaGetLastError();
         ++*kernels;
     }
-    if (err == cudaSuccess && ev1) err = cudaEventRecord(ev1, st);
+    if (err == cudaSuccess && ev1) err = cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal);
     bool partials = false;
     if (err == cudaSuccess && p.sample_every > 0 && !p.obs_skip) {
         if (e->pair) {
@@ -2590,7 +2590,7 @@ cudaError_t engine_run_steps(EngineState *e, const StepParams &p, const DevBuffe
     *kernels = 0;
     if (e->engine != TTS_ENGINE_RESIDENT) return cudaErrorNotSupported;
     cudaError_t err = cudaSuccess;
-    if (ev0) err = cudaEventRecord(ev0, st);
+    if (ev0) err = cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal);
     auto fill = [&](auto &a) {
         a.species = b.species;
         a.atom = b.atom;
@@ -2675,7 +2675,7 @@ cudaError_t engine_run_steps(EngineState *e, const StepParams &p, const DevBuffe
         *kernels += 3;
         done += chunk;
     }
-    if (err == cudaSuccess && ev1) err = cudaEventRecord(ev1, st);
+    if (err == cudaSuccess && ev1) err = cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal);
     return err;
 }
 

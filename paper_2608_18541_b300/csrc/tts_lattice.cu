@@ -557,7 +557,7 @@ cudaError_t lattice_record_step(tts_system *s, cudaStream_t st, int *kernels, cu
     LatticeState *L = s->lat;
     *kernels = 0;
     cudaError_t e = cudaSuccess;
-    if (ev0) e = cudaEventRecord(ev0, st);
+    if (ev0) e = cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal);
     const double coef = L->dtL / (2.0 * L->mass);
     if (e == cudaSuccess) { e = launch_sigma(s->p, s->b, s->ncells_total, s->precision, st); ++*kernels; }
     if (e == cudaSuccess) { e = per_atom(s, st, 0, coef); ++*kernels; }
@@ -605,7 +605,7 @@ cudaError_t lattice_record_step(tts_system *s, cudaStream_t st, int *kernels, cu
         e = cudaGetLastError();
         ++*kernels;
     }
-    if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, st);
+    if (e == cudaSuccess && ev1) e = cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal);
     return e;
 }
 

@@ -256,7 +256,7 @@ cudaError_t record_step(tts_system *s, cudaStream_t c, int *kernels, cudaEvent_t
         e = launch_sigma(s->p, s->b, s->ncells_total, s->precision, c);
         ++*kernels;
     }
-    if (e == cudaSuccess && ev0) e = cudaEventRecord(ev0, c);
+    if (e == cudaSuccess && ev0) e = cudaEventRecordWithFlags(ev0, c, cudaEventRecordExternal);
     for (int pass = 0; pass < s->max_passes && e == cudaSuccess; ++pass) {
         const int64_t off = s->pass_offset[pass];
         const int nr = static_cast<int>(s->pass_offset[pass + 1] - off);
@@ -264,7 +264,7 @@ cudaError_t record_step(tts_system *s, cudaStream_t c, int *kernels, cudaEvent_t
                                 sweep_ctl(s, pass, s->max_passes));
         ++*kernels;
     }
-    if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, c);
+    if (e == cudaSuccess && ev1) e = cudaEventRecordWithFlags(ev1, c, cudaEventRecordExternal);
     e = (e == cudaSuccess) ? step_tail(p, s->b, s->tp, s->ttm_active, s->n_inst, s->precision, s->obs_blocks, c, kernels)
                            : e;
     return e;
@@ -992,18 +992,41 @@ int tts_step(tts_system *s, int64_t nsteps)
         return TTS_OK;
     }
     if (s->profiling) {
-        for (int64_t i = 0; i < nsteps; ++i) {
-            cudaEvent_t ev[2];
-            TTS_CUDA(cudaEventCreate(&ev[0]), "profile event");
-            TTS_CUDA(cudaEventCreate(&ev[1]), "profile event");
-            s->prof_events.push_back(ev[0]);
-            s->prof_events.push_back(ev[1]);
+        // The steps, with timing events around their colour passes, are
+        // captured into one graph and replayed: the device runs them back to
+        // back as in the timed path, instead of waiting on the host's launches
+        // between kernels.  Every kernel is a node of its own (no step graph
+        // is reused), so the launch count stays exact.
+        cudaStream_t c = s->capture;
+        TTS_CUDA(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal), "begin profiled capture");
+        cudaError_t e = cudaSuccess;
+        int total = 0;
+        for (int64_t i = 0; i < nsteps && e == cudaSuccess; ++i) {
+            cudaEvent_t ev[2] = {nullptr, nullptr};
+            e = cudaEventCreate(&ev[0]);
+            if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+            if (ev[0]) s->prof_events.push_back(ev[0]);
+            if (ev[1]) s->prof_events.push_back(ev[1]);
+            if (e != cudaSuccess) break;
             s->prof_pair_steps.push_back(1);
             int kernels = 0;
-            cudaError_t e = record_step(s, s->stream, &kernels, ev[0], ev[1], true);
-            if (e != cudaSuccess) return cuda_fail(e, "profiled step");
-            s->launches += kernels;
+            e = record_step(s, c, &kernels, ev[0], ev[1], true);
+            total += kernels;
         }
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(c, &g);
+        if (e == cudaSuccess) e = e2;
+        cudaGraphExec_t x = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e == cudaSuccess) e = cudaGraphLaunch(x, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);   // before the executable graph goes
+        if (x) cudaGraphExecDestroy(x);
+        if (e != cudaSuccess) {
+            drop_profile_events(s);
+            return cuda_fail(e, "profiled steps");
+        }
+        s->launches += total;
         return TTS_OK;
     }
     if (s->dirty) {
