@@ -293,6 +293,95 @@ def fused_leg(P, g, args, stream, spins, peak, peak_kind):
 
 
 # ---------------------------------------------------------------------------
+# The other workloads of the benchmark suite, each timed on the GPU and
+# compared with the FP64 oracle over a short window from the same initial
+# state: bcc Fe 10^3 (FP64), GdFeCo 32^3 with a one-cell 2TM (FP64 and FP32)
+# and the moving bcc Fe 40^3 lattice (FP32 spins, FP64 TTM).
+# ---------------------------------------------------------------------------
+def _suite(W):
+    """(name, system, ttm, lattice, precisions, timed steps, parity steps, unit)
+    of each suite workload; the moving lattice's steps are lattice steps of 10
+    spin sub-steps, and its source power is given (no calibration run)."""
+    c1 = W.config_bcc_fe_2000()
+    c2, t2 = W.config_gdfeco_32()
+    c4, t4, l4 = W.config_moving_fe(40)
+    t4 = dict(t4, source="power", P0=2e21)
+    return [
+        ("bcc Fe 10^3 cells (2000 spins), Bethe-Slater NN+NNN, 300 K, no TTM", c1, None, None, (64,), 1000, 200, 1),
+        ("GdFeCo sc 32^3 (32768 spins), one-cell 2TM, 50 fs pulse to 1500 K", c2, t2, None, (64, 32), 2000, 200, 1),
+        ("moving bcc Fe 40^3 cells (128000 atoms), Morse + magneto-mechanical force, 10x10x40 TTM, "
+         "100 fs pulse, source power 2e21 W/m^3", c4, t4, l4, (32,), 10, 2, 10),
+    ]
+
+
+def _oracle_suite(q):
+    """Oracle spins after each suite workload's parity window (spawned process)."""
+    import oracle as O
+    from paper_2608_18541_b300 import workloads as W
+    out = []
+    for name, sysd, ttm, lat, precs, steps, psteps, sub in _suite(W):
+        t0 = time.perf_counter()
+        o = O.Oracle(sysd, ttm, lattice=lat)
+        if lat is not None:
+            o.lattice_step(psteps)
+        else:
+            o.step(psteps)
+        out.append((o.spins(), time.perf_counter() - t0))
+    q.put(out)
+
+
+class OracleSuite:
+    def __init__(self):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.q = ctx.Queue()
+        self.proc = ctx.Process(target=_oracle_suite, args=(self.q,))
+        self.proc.start()
+
+    def result(self, timeout=3600):
+        r = self.q.get(timeout=timeout)
+        self.proc.join()
+        return r
+
+
+def suite_leg(P, W, stream, oracle):
+    """Throughput and FP64-oracle parity of the suite workloads on the GPU."""
+    import numpy as np
+    import torch
+    gpu = []
+    for name, sysd, ttm, lat, precs, steps, psteps, sub in _suite(W):
+        for prec in precs:
+            g = P.System(sysd, ttm, precision=prec, stream=stream.cuda_stream, lattice=lat)
+            g.step(psteps)
+            got = g.get_spins(0)
+            g.step(max(1, steps // 10))
+            g.sync()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            gpu.append((name, prec, g.engine, g.n_total, steps, sub, ms, psteps, got))
+            del g
+    want = oracle.result()
+    idx = {n: k for k, (n, *_rest) in enumerate(_suite(W))}
+    out = []
+    for name, prec, engine, n, steps, sub, ms, psteps, got in gpu:
+        ref, osec = want[idx[name]]
+        tol = 1e-10 if prec == 64 else 2e-5
+        err = float(np.abs(got - ref).max())
+        out.append({"workload": name, "precision": "f%d" % prec, "engine": engine, "spins": n,
+                    "value": n * steps * sub / (ms / 1e3), "unit": "spin-steps/s",
+                    "timed": "%d %s" % (steps, "lattice steps (x%d spin sub-steps)" % sub if sub > 1 else "steps"),
+                    "parity": {"max_abs_ds": err, "tolerance": tol, "pass": err <= tol,
+                               "steps": psteps if sub == 1 else "%d lattice steps" % psteps,
+                               "against": "FP64 CPU oracle, same seeds, per spin component"}})
+    return out
+
+
+# ---------------------------------------------------------------------------
 # The FP64 CPU oracle on the host cores, the paper's task-level strategy: one
 # single-threaded process per realisation, all running at once.  Everything
 # here runs in spawned interpreters (no CUDA state is ever forked).
@@ -471,6 +560,7 @@ def main():
                          "'last': the last one offered, for the FP32 checker the fused sweep at the cost "
                          "model's fusion depth)")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-suite", action="store_true", help="skip the other workloads of the suite")
     ap.add_argument("--no-merged", action="store_true")
     args = ap.parse_args()
 
@@ -589,6 +679,7 @@ def main():
     camp = None
     if world == 1 and not args.no_cpu_baseline:
         camp = OracleCampaign(sysd, ttm, _pool_size(args.cpu_procs), 1, args.cpu_steps, args.parity_steps)
+    osuite = OracleSuite() if world == 1 and not args.no_suite else None
 
     peak, peak_kind = _peaks()
     bpu = BYTES_PER_SPIN_STEP[args.precision]
@@ -612,6 +703,7 @@ def main():
     fused = None
     if world == 1 and not args.no_fused:
         fused = fused_leg(P, g, args, stream, spins, peak, peak_kind)
+    suite = suite_leg(P, W, stream, osuite) if osuite is not None else None
     single = None
     if world == 1 and not args.no_single and args.workload == "gdfeco_128x4":
         single = [single_leg(P, W, n, args, stream, peak, peak_kind) for n in (128, 256)]
@@ -643,7 +735,7 @@ def main():
                    else "working set may fit L2", "parallelism": "instances sharded, dp%d" % world},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clocks, "parity": parity, "single_instance": single, "fused_sweep": fused, "ensemble": ens,
-        "merged_sweep": merged,
+        "merged_sweep": merged, "suite": suite,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -91,22 +91,31 @@ __device__ __forceinline__ R *arr(void *p, int c, int64_t n)
     return static_cast<R *>(p) + int64_t(c) * n;
 }
 
-__device__ __forceinline__ double bethe_slater(double r, double J1, double J2, double J3)
+__device__ __forceinline__ float mul_rn(float x, float y) { return __fmul_rn(x, y); }
+__device__ __forceinline__ double mul_rn(double x, double y) { return __dmul_rn(x, y); }
+
+// Bethe-Slater J(r) and its derivative, and the Morse force magnitude, in the
+// spin precision R (FP32 systems compute their pair forces and exchange table
+// in FP32; the force sums stay FP64).
+template <typename R>
+__device__ __forceinline__ R bethe_slater_dr_r(R r, R J1, R J2, R J3)
 {
-    const double x = (r / J3) * (r / J3);
-    return 4.0 * J1 * x * (1.0 - J2 * x) * exp(-x);
+    const R x = (r / J3) * (r / J3);
+    return R(4) * J1 * exp(-x) * (R(1) - R(2) * J2 * x - x + J2 * x * x) * R(2) * r / (J3 * J3);
 }
 
-__device__ __forceinline__ double bethe_slater_dr(double r, double J1, double J2, double J3)
+template <typename R>
+__device__ __forceinline__ R bethe_slater_r(R r, R J1, R J2, R J3)
 {
-    const double x = (r / J3) * (r / J3);
-    return 4.0 * J1 * exp(-x) * (1.0 - 2.0 * J2 * x - x + J2 * x * x) * 2.0 * r / (J3 * J3);
+    const R x = (r / J3) * (r / J3);
+    return R(4) * J1 * x * (R(1) - J2 * x) * exp(-x);
 }
 
-__device__ __forceinline__ double morse_dU_raw(const LatArgs &a, double r)
+template <typename R>
+__device__ __forceinline__ R morse_dU_raw_r(const LatArgs &a, R r)
 {
-    const double e1 = exp(-a.morse_alpha * (r - a.morse_r0));
-    return 2.0 * a.morse_alpha * a.morse_D * (e1 - e1 * e1);
+    const R e1 = exp(-R(a.morse_alpha) * (r - R(a.morse_r0)));
+    return R(2) * R(a.morse_alpha) * R(a.morse_D) * (e1 - e1 * e1);
 }
 
 __device__ __forceinline__ double morse_U_raw(const LatArgs &a, double r)
@@ -160,21 +169,23 @@ __global__ void refresh_kernel(LatArgs a, DevBuffers b, int precision_is_64)
         const int tj = b.species[j];
         const int kind = a.ex.kind[ti][tj];
         if (kind == TTS_EXCH_NONE) continue;
-        const double dx = double(cv<R>(a, 0, k, i)) + double(ux[j]) - double(ux[i]);
-        const double dy = double(cv<R>(a, 1, k, i)) + double(uy[j]) - double(uy[i]);
-        const double dz = double(cv<R>(a, 2, k, i)) + double(uz[j]) - double(uz[i]);
-        const double r = sqrt(dx * dx + dy * dy + dz * dz);
-        if (!(r < a.ex.rc[ti][tj])) continue;
-        const double J = kind == TTS_EXCH_CONST ? a.ex.J1[ti][tj]
-                                                : bethe_slater(r, a.ex.J1[ti][tj], a.ex.J2[ti][tj], a.ex.J3[ti][tj]);
-        if (J == 0.0) continue;
+        const R dx = cv<R>(a, 0, k, i) + (ux[j] - ux[i]);
+        const R dy = cv<R>(a, 1, k, i) + (uy[j] - uy[i]);
+        const R dz = cv<R>(a, 2, k, i) + (uz[j] - uz[i]);
+        const R r = sqrt(dx * dx + dy * dy + dz * dz);
+        if (!(r < R(a.ex.rc[ti][tj]))) continue;
+        // J(r) / mu_i in the spin precision (tesla), J1 / mu_i folded first
+        const R J = kind == TTS_EXCH_CONST
+                        ? R(a.ex.J1[ti][tj] * a.inv_mu[ti])
+                        : bethe_slater_r<R>(r, R(a.ex.J1[ti][tj] * a.inv_mu[ti]), R(a.ex.J2[ti][tj]), R(a.ex.J3[ti][tj]));
+        if (J == R(0)) continue;
         if (a.colour[i] == a.colour[j]) atomicOr(b.health, kHealthColour);
         if (cnt >= a.zmax) {
             atomicOr(b.health, kHealthOverflow);
             break;
         }
         b.nbr[int64_t(cnt) * a.n + i] = j;
-        w[int64_t(cnt) * a.n + i] = static_cast<R>(J * a.inv_mu[ti]);
+        w[int64_t(cnt) * a.n + i] = J;
         ++cnt;
     }
     for (; cnt < a.zmax; ++cnt) {
@@ -207,32 +218,47 @@ __global__ void force_kernel(LatArgs a, DevBuffers b)
     const R *ux = arr<R>(a.u, 0, a.n), *uy = arr<R>(a.u, 1, a.n), *uz = arr<R>(a.u, 2, a.n);
     const R *S0 = static_cast<const R *>(b.sx), *S1 = static_cast<const R *>(b.sy), *S2 = static_cast<const R *>(b.sz);
     const int ti = b.species[i];
-    const double si0 = S0[i], si1 = S1[i], si2 = S2[i];
-    double fx = 0.0, fy = 0.0, fz = 0.0;
+    const R si0 = S0[i], si1 = S1[i], si2 = S2[i];
+    const R uxi = ux[i], uyi = uy[i], uzi = uz[i];
+    // pair terms in the spin precision, energies in units of 1e-20 J inside
+    // the loop so that FP32 stays far from its range limits; the sums are
+    // compensated (each addition's rounding error carried in a second word,
+    // Knuth's TwoSum), which keeps their rounding near that of FP64 sums at
+    // the spin precision's rate.  Products are rounded before they are
+    // added (no fused multiply-add), as TwoSum assumes.
+    const R morse_rc = R(a.morse_rc), dU_rc = R(a.dU_rc * 1e20);
+    R fx = R(0), fy = R(0), fz = R(0), ex = R(0), ey = R(0), ez = R(0);
+    auto two_sum = [](R &sum, R &err, R v) {
+        const R t = sum + v;
+        const R bp = t - sum;
+        err += (sum - (t - bp)) + (v - bp);
+        sum = t;
+    };
     for (int k = 0; k < a.zc; ++k) {
         const int j = a.cand[int64_t(k) * a.n + i];
         if (j < 0) break;
-        const double dx = double(cv<R>(a, 0, k, i)) + double(ux[j]) - double(ux[i]);
-        const double dy = double(cv<R>(a, 1, k, i)) + double(uy[j]) - double(uy[i]);
-        const double dz = double(cv<R>(a, 2, k, i)) + double(uz[j]) - double(uz[i]);
-        const double r = sqrt(dx * dx + dy * dy + dz * dz);
-        double g = 0.0;                                  // dE_pair/dr, J per angstrom
-        if (r < a.morse_rc) g += morse_dU_raw(a, r) - a.dU_rc;
+        const R dx = cv<R>(a, 0, k, i) + (ux[j] - uxi);
+        const R dy = cv<R>(a, 1, k, i) + (uy[j] - uyi);
+        const R dz = cv<R>(a, 2, k, i) + (uz[j] - uzi);
+        const R r = sqrt(dx * dx + dy * dy + dz * dz);
+        R g = R(0);                                      // dE_pair/dr, 1e-20 J per angstrom
+        if (r < morse_rc) g += morse_dU_raw_r<R>(a, r) * R(1e20) - dU_rc;
         const int tj = b.species[j];
-        if (a.ex.kind[ti][tj] == TTS_EXCH_BETHE_SLATER && r < a.ex.rc[ti][tj]) {
-            const double ss = si0 * double(S0[j]) + si1 * double(S1[j]) + si2 * double(S2[j]);
-            g -= bethe_slater_dr(r, a.ex.J1[ti][tj], a.ex.J2[ti][tj], a.ex.J3[ti][tj]) * ss;
+        if (a.ex.kind[ti][tj] == TTS_EXCH_BETHE_SLATER && r < R(a.ex.rc[ti][tj])) {
+            const R ss = si0 * S0[j] + si1 * S1[j] + si2 * S2[j];
+            g -= bethe_slater_dr_r<R>(r, R(a.ex.J1[ti][tj] * 1e20), R(a.ex.J2[ti][tj]), R(a.ex.J3[ti][tj])) * ss;
         }
-        if (g != 0.0) {
-            const double s = g * 1e10 / r;               // N per angstrom of separation
-            fx += s * dx;
-            fy += s * dy;
-            fz += s * dz;
+        if (g != R(0)) {
+            const R s = g / r;                           // 1e-20 J per angstrom^2
+            two_sum(fx, ex, mul_rn(s, dx));
+            two_sum(fy, ey, mul_rn(s, dy));
+            two_sum(fz, ez, mul_rn(s, dz));
         }
     }
-    arr<R>(a.f, 0, a.n)[i] = static_cast<R>(fx);
-    arr<R>(a.f, 1, a.n)[i] = static_cast<R>(fy);
-    arr<R>(a.f, 2, a.n)[i] = static_cast<R>(fz);
+    // 1e-20 J per angstrom = 1e-10 N
+    arr<R>(a.f, 0, a.n)[i] = static_cast<R>((double(fx) + double(ex)) * 1e-10);
+    arr<R>(a.f, 1, a.n)[i] = static_cast<R>((double(fy) + double(ey)) * 1e-10);
+    arr<R>(a.f, 2, a.n)[i] = static_cast<R>((double(fz) + double(ez)) * 1e-10);
 }
 
 // second half kick, then the Ornstein-Uhlenbeck electron-ion coupling
@@ -274,23 +300,39 @@ __global__ void kick_ou_kernel(LatArgs a, DevBuffers b, double coef)
 
 // TTM of a moving lattice: ion energy handed over, then diffusion and the
 // source over dtL in sub-steps (no G term: the ions couple through their own
-// friction and noise).  One block per instance.
-__global__ void lattice_ttm_kernel(LatArgs a, DevBuffers b, TtmParams tp)
+// friction and noise).  One cluster of kLatTtmCtas CTAs per instance (16, the
+// largest cluster the part allows with the non-portable size), each CTA
+// a contiguous range of its cells: the grid's FP64 work spreads over that many
+// SMs (one SM's FP64 rate made a single block take ~0.9 ms a lattice step on
+// a 10 x 10 x 40 grid with 13 sub-steps).  T_e and the increments live in
+// global memory; cluster barriers (release / acquire) order the phases.
+constexpr int kLatTtmCtas = 16;
+constexpr int kLatTtmThreads = 256;
+
+__device__ __forceinline__ void lat_cluster_sync()
 {
-    const DevInstance I = b.inst[blockIdx.x];
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kLatTtmThreads) lattice_ttm_kernel(LatArgs a, DevBuffers b, TtmParams tp)
+{
+    const int inst = static_cast<int>(blockIdx.x) / kLatTtmCtas, rank = static_cast<int>(blockIdx.x) % kLatTtmCtas;
+    const DevInstance I = b.inst[inst];
     const int nc = I.ncells;
+    const int c0 = static_cast<int>(int64_t(rank) * nc / kLatTtmCtas);
+    const int c1 = static_cast<int>(int64_t(rank + 1) * nc / kLatTtmCtas);
     double *Te = b.Te + I.cell_begin;
     double *dE = b.ttm_scratch + I.cell_begin;
     const double *shape = b.src_shape + I.cell_begin;
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    for (int c = c0 + static_cast<int>(threadIdx.x); c < c1; c += blockDim.x) {
         const long long q = a.cell_acc[I.cell_begin + c];
         a.cell_acc[I.cell_begin + c] = 0;
         if (q != 0) {
             const double Ee = 0.5 * tp.gamma_e * Te[c] * Te[c] + (double(q) / kFixScale) / I.cell_volume;
-            Te[c] = sqrt(2.0 * Ee / tp.gamma_e);
+            Te[c] = sqrt(2.0 * Ee * tp.inv_gamma_e);
         }
     }
-    __syncthreads();
+    lat_cluster_sync();
     const int64_t ls = *a.lstep;
     const double delta = a.dtL / I.substeps;
     double deposited = 0.0;
@@ -302,36 +344,51 @@ __global__ void lattice_ttm_kernel(LatArgs a, DevBuffers b, TtmParams tp)
             const double z = (t - I.t0) / I.sigma_t;
             pulse = I.P0 * exp(-0.5 * z * z);
         }
-        for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        for (int c = c0 + static_cast<int>(threadIdx.x); c < c1; c += blockDim.x) {
             const int cx = c % nxc, cy = (c / nxc) % nyc, cz = c / (nxc * nyc);
             const double Tc = Te[c];
             double lap = 0.0;
             if (nxc > 1)
-                lap += (Te[(cz * nyc + cy) * nxc + (cx + 1) % nxc] - 2.0 * Tc + Te[(cz * nyc + cy) * nxc + (cx + nxc - 1) % nxc]) /
-                       (I.dx[0] * I.dx[0]);
+                lap += (Te[(cz * nyc + cy) * nxc + (cx + 1) % nxc] - 2.0 * Tc + Te[(cz * nyc + cy) * nxc + (cx + nxc - 1) % nxc]) *
+                       I.inv_dx2[0];
             if (nyc > 1)
-                lap += (Te[(cz * nyc + (cy + 1) % nyc) * nxc + cx] - 2.0 * Tc + Te[(cz * nyc + (cy + nyc - 1) % nyc) * nxc + cx]) /
-                       (I.dx[1] * I.dx[1]);
+                lap += (Te[(cz * nyc + (cy + 1) % nyc) * nxc + cx] - 2.0 * Tc + Te[(cz * nyc + (cy + nyc - 1) % nyc) * nxc + cx]) *
+                       I.inv_dx2[1];
             if (nzc > 1)
                 lap += (Te[(((cz + 1) % nzc) * nyc + cy) * nxc + cx] - 2.0 * Tc +
-                        Te[(((cz + nzc - 1) % nzc) * nyc + cy) * nxc + cx]) / (I.dx[2] * I.dx[2]);
+                        Te[(((cz + nzc - 1) % nzc) * nyc + cy) * nxc + cx]) * I.inv_dx2[2];
             const double src = pulse * shape[c];
             dE[c] = delta * (tp.kappa_e * lap + src);
             deposited += delta * src * I.cell_volume;
         }
-        __syncthreads();
-        for (int c = threadIdx.x; c < nc; c += blockDim.x)
-            Te[c] = sqrt(2.0 * (0.5 * tp.gamma_e * Te[c] * Te[c] + dE[c]) / tp.gamma_e);
-        __syncthreads();
+        lat_cluster_sync();
+        for (int c = c0 + static_cast<int>(threadIdx.x); c < c1; c += blockDim.x)
+            Te[c] = sqrt(2.0 * (0.5 * tp.gamma_e * Te[c] * Te[c] + dE[c]) * tp.inv_gamma_e);
+        lat_cluster_sync();
     }
-    __shared__ double red[256];
+    // source energy deposited: threads in a fixed tree, then the CTAs in rank
+    // order by CTA 0 through distributed shared memory
+    __shared__ double red[kLatTtmThreads];
     red[threadIdx.x] = deposited;
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    for (int h = kLatTtmThreads / 2; h > 0; h >>= 1) {
+        if (static_cast<int>(threadIdx.x) < h) red[threadIdx.x] += red[threadIdx.x + h];
         __syncthreads();
     }
-    if (threadIdx.x == 0) b.src_energy[blockIdx.x] += red[0];
+    lat_cluster_sync();
+    if (rank == 0 && threadIdx.x == 0) {
+        double tot = 0.0;
+        const uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(&red[0]));
+        for (int r = 0; r < kLatTtmCtas; ++r) {
+            uint32_t remote;
+            double v;
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(r));
+            asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(remote) : "memory");
+            tot += v;
+        }
+        b.src_energy[inst] += tot;
+    }
+    lat_cluster_sync();        // no CTA leaves while CTA 0 may still read its partial
 }
 
 // kinetic and pair energies per observable block (sampling steps only)
@@ -584,8 +641,20 @@ cudaError_t lattice_record_step(tts_system *s, cudaStream_t st, int *kernels, cu
     if (e == cudaSuccess) { e = per_atom(s, st, 3); ++*kernels; }
     if (e == cudaSuccess) { e = per_atom(s, st, 4, coef); ++*kernels; }
     if (e == cudaSuccess && s->ttm_active) {
-        lattice_ttm_kernel<<<s->n_inst, 256, 0, st>>>(make_args(s), s->b, s->tp);
-        e = cudaGetLastError();
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(static_cast<unsigned>(s->n_inst * kLatTtmCtas));
+        cfg.blockDim = dim3(kLatTtmThreads);
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = kLatTtmCtas;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        e = cudaFuncSetAttribute(lattice_ttm_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, lattice_ttm_kernel, make_args(s), s->b, s->tp);
+        if (e == cudaSuccess) e = cudaGetLastError();
         ++*kernels;
     }
     if (e == cudaSuccess && s->desc.sample_every > 0) {

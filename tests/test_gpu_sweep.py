@@ -21,7 +21,7 @@ FS = 1e-15
 def _launches_per_step(g, n=4):
     g.set_step(1000)                  # the same sampling phase for every measurement
     a = g.info().kernel_launches
-    g.profile_enable(True)            # direct launches, so that every kernel is counted
+    g.profile_enable(True)            # every kernel its own graph node, so that each is counted
     g.step(n)
     g.sync()
     g.profile_enable(False)
