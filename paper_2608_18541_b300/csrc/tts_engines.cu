@@ -2108,12 +2108,26 @@ int engine_create(const tts_system_desc &d, const std::vector<HostInstance> &hos
                 if (bx <= std::max(32, hxs))
                     for (int threads : {128, 256}) e->configs.push_back({bx, threads / bx});
         } else {
-            e->bx = hxs >= 128 ? 128 : (hxs >= 64 ? 64 : 32);
-            e->by = 256 / e->bx;
-            for (int bx : {32, 64, 128})
-                if (bx <= std::max(32, hxs))
-                    for (int threads : {128, 256})
-                        if (threads / bx >= 1) e->configs.push_back({bx, threads / bx});
+            // FP64: a row of at most hx sites a block row, and blocks small
+            // enough that every SM gets one (a pass's FP64 work runs at the
+            // FP64 rate of the SMs it lands on: on 32^3, 256-thread blocks
+            // filled 128 SMs half-idle).
+            int bx = 128;
+            while (bx > 8 && bx > hxs) bx >>= 1;
+            const int nsm = e->sm_count > 0 ? e->sm_count : 148;
+            auto nblocks = [&](int threads) {
+                const int64_t rows = (e->shape[1] + threads / bx - 1) / (threads / bx);
+                return int64_t((hxs + bx - 1) / bx) * rows * e->shape[2] * e->n_inst;
+            };
+            int threads = 256;
+            while (threads > std::max(32, bx) && nblocks(threads) < nsm) threads >>= 1;
+            e->bx = bx;
+            e->by = threads / bx;
+            e->configs.push_back({e->bx, e->by});
+            for (int cbx : {32, 64, 128})
+                if (cbx <= std::max(32, hxs))
+                    for (int t : {128, 256})
+                        if (t / cbx >= 1 && !(cbx == e->bx && t / cbx == e->by)) e->configs.push_back({cbx, t / cbx});
         }
         // the default first
         for (size_t k = 0; k < e->configs.size(); ++k)

@@ -580,12 +580,38 @@ cudaError_t launch_calibrate(const CalibJob *jobs_dev, const double *cand_dev, d
 // a SM, so a few thousand cells in 256-thread blocks would occupy a tenth of
 // the SMs: take the largest power of two in [32, 256] that still gives a
 // block to each of the 148 SMs.  Each thread computes the same cell either way.
-static int cell_block(int64_t n)
+// SMs of the current device (cached per device; 148 when it cannot be read).
+static int device_sms()
 {
-    int bs = 256;
-    while (bs > 32 && (n + bs - 1) / bs < 148) bs >>= 1;
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 148;
+    }
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            n = 148;
+        }
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
+// Threads a block for n independent work items: the largest of bs, bs/2, ...
+// (down to one warp) that still gives every SM a block, so that a small
+// launch spreads over the GPU instead of filling a few SMs (FP64 work runs
+// at the FP64 rate of the SMs it lands on).
+static int spread_block(int64_t n, int bs)
+{
+    const int sms = device_sms();
+    while (bs > 32 && (n + bs - 1) / bs < sms) bs >>= 1;
     return bs;
 }
+
+static int cell_block(int64_t n) { return spread_block(n, 256); }
 
 cudaError_t launch_sigma(const StepParams &p, const DevBuffers &b, int ncells, int precision, cudaStream_t st)
 {
@@ -602,7 +628,7 @@ cudaError_t launch_pass_general(const StepParams &p, const DevBuffers &b, int pr
                                 SweepCtl sw)
 {
     if (nwork <= 0) return cudaSuccess;
-    const int bs = block;
+    const int bs = spread_block(nwork, block);
     const int64_t gs = (nwork + bs - 1) / bs;
     if (precision == 64)
         pass_general_kernel<double><<<gs, bs, 0, st>>>(p, b, pass, b.ranges + range_offset, nranges, nwork, sw);
