@@ -353,10 +353,13 @@ TTS_API int tts_set_state(tts_system *sys, const void *buf, size_t nbytes);
 
 TTS_API int tts_info(tts_system *sys, tts_info_t *info);
 
-/* Kernel timing.  While enabled, tts_step launches each step's kernels one by
- * one instead of replaying the captured graph, and brackets the step's
- * dominant kernels (the colour passes, or the fused step kernel of a fast
- * engine) with CUDA events on the system's stream.  No work is skipped. */
+/* Kernel timing.  While enabled, tts_step records each call's steps, with
+ * CUDA events around every step's dominant kernels (the colour passes, or
+ * the fused step kernel of a fast engine), into a graph of their own (every
+ * kernel a node, none of the cached step graphs) and replays it on the
+ * system's stream, waiting for it before it returns; the resident engine
+ * brackets its multi-step launch instead.  No work is skipped and the results
+ * are those of the unprofiled path. */
 TTS_API int tts_profile_enable(tts_system *sys, int enable);
 /* Total duration in ms of the bracketed kernels since profiling was enabled,
  * the number of steps bracketed, and the spin-steps those steps completed
@@ -393,8 +396,9 @@ TTS_API int tts_ttm_advance_noalloc(const tts_ttm_desc *t, const double box_ang[
                                     double *dev_Te, double *dev_Tl, double *dev_deposited, void *stream);
 
 /* Autotuner: time every launch configuration the system's engine offers
- * (block shapes of the colour-pass kernels; threads per CTA of the resident
- * kernel) over probe_steps steps each, starting every probe from the same
+ * (block shapes of the colour-pass kernels, the instance chains of the FP32
+ * checker's separate passes, the fused sweep at each fusion depth; threads
+ * per CTA of the resident kernel) over probe_steps steps each, starting every probe from the same
  * saved state and restoring it afterwards, and keep the fastest.  Choices are
  * cached per engine, precision and shape for the life of the process.
  * *chosen (may be NULL) receives the index of the configuration kept and
