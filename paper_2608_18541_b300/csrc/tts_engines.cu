@@ -181,6 +181,7 @@ struct PairArgs {
     const int *cur;              // 1: the current state is in S1, else in S
     const int *cell;             // general slot -> TTM cell
     const float *sigma;          // [cell][species][h]
+    uint32_t sigma_odd;          // elements from sigma to the table of odd steps (0: one table)
     const int64_t *step;
     unsigned int *health;
     PairConsts k;
@@ -346,7 +347,7 @@ template <bool AXZ, int CM = kCellAny>
 __device__ __forceinline__ void pair_finish(const PairArgs &a, const PairSite &p, int colour, int hsel, bool h2, f2 g1,
                                             f2 g2, f2 g3, f2 htx, f2 hty, f2 htz, f2 h1x, f2 h1y, f2 h1z,
                                             ulonglong2 olo, ulonglong2 ohi, ulonglong2 *Wlo, ulonglong2 *Whi,
-                                            uint32_t q)
+                                            uint32_t q, uint32_t step)
 {
     f2 sx{olo.x}, sy{olo.y}, sz{ohi.x};
     const f2 w{ohi.y};
@@ -357,7 +358,8 @@ __device__ __forceinline__ void pair_finish(const PairArgs &a, const PairSite &p
         const int tA = wA != 0.0f ? 1 : 0, tB = wB != 0.0f ? 1 : 0;
         int cA, cB;
         pair_cells<CM>(a, p, colour, cA, cB);
-        sig = f2_make(a.sigma[(cA * TTS_MAX_SPECIES + tA) * 2 + hsel], a.sigma[(cB * TTS_MAX_SPECIES + tB) * 2 + hsel]);
+        const float *tab = a.sigma + (step & 1u) * a.sigma_odd;
+        sig = f2_make(tab[(cA * TTS_MAX_SPECIES + tA) * 2 + hsel], tab[(cB * TTS_MAX_SPECIES + tB) * 2 + hsel]);
     }
     pair_update<AXZ>(sx, sy, sz, htx, hty, htz, h1x, h1y, h1z, w, a.noise != 0, sig, g1, g2, g3, a.k, h2);
     float sA, sB;
@@ -401,8 +403,9 @@ __device__ __forceinline__ void pair_block(const PairArgs &a, int colour, int hs
     }
     if (y2 >= Ly2 || kx >= hx) return;
     const PairSite p = make_site(a, inst, z, y2, kx, colour);
+    const uint32_t step = static_cast<uint32_t>(*a.step);
     f2 g1{0}, g2{0}, g3{0};
-    if (a.noise) site_noise(a, p, static_cast<uint32_t>(*a.step), pass, g1, g2, g3);
+    if (a.noise) site_noise(a, p, step, pass, g1, g2, g3);
     ulonglong2 *base = pair_state(a) + int64_t(inst) * a.n_inst_sites;
     const ulonglong2 *Olo = base + (colour ? 0 : a.nhalf);
     const ulonglong2 *Ohi = Olo + a.npair;
@@ -416,7 +419,7 @@ __device__ __forceinline__ void pair_block(const PairArgs &a, int colour, int hs
                    (z * Ly2 + yp) * hx, (z * Ly2 + ym) * hx, htx, hty, htz, h1x, h1y, h1z);
     const uint32_t q = r0 + kx;
     pair_finish<AXZ, CM>(a, p, colour, hsel, h2, g1, g2, g3, htx, hty, htz, h1x, h1y, h1z, Wlo[q], Whi[q], Wlo, Whi,
-                         q);
+                         q, step);
 }
 
 // SW: the launch is a leading or trailing pass of the merged sweep (compiled
@@ -574,7 +577,7 @@ __global__ void __launch_bounds__(256, 3) checker_pair_tiled_kernel(PairArgs a, 
                 const uint32_t qs = ty * hx + tx;
                 const uint32_t q = (z * Ly2 + y0 + ty) * hx + tx;
                 pair_finish<AXZ>(a, p, colour, hsel, h2, g1, g2, g3, htx, hty, htz, h1x, h1y, h1z, Tw[qs],
-                                 Tw[tw + qs], gw, gw + a.npair, q);
+                                 Tw[tw + qs], gw, gw + a.npair, q, step);
             }
             ++c_o;
             ++c_w;
@@ -1705,8 +1708,9 @@ struct EngineState {
     // boundary overlaps another group's pass
     int chains = 1;
     static constexpr int kMaxChains = 4;
-    cudaStream_t side[kMaxChains - 1] = {};
+    cudaStream_t side[kMaxChains] = {};      // chains 2.. and the TTM branch
     cudaEvent_t ev_fork = nullptr, ev_join[kMaxChains - 1] = {};
+    cudaEvent_t ev_ttm = nullptr;    // the step's TTM, run beside the chains
     // resident
     ResInst *ri = nullptr;
     int *order = nullptr;
@@ -2149,10 +2153,12 @@ int engine_create(const tts_system_desc &d, const std::vector<HostInstance> &hos
             // (the colour passes alone 150 -> 139 us), four 143 us.  With two
             // or more instances two chains become the default.
             if (e->n_inst >= 2) {
-                bool ok = cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming) == cudaSuccess;
-                for (int c = 0; ok && c < EngineState::kMaxChains - 1; ++c)
+                bool ok = cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+                          cudaEventCreateWithFlags(&e->ev_ttm, cudaEventDisableTiming) == cudaSuccess;
+                for (int c = 0; ok && c < EngineState::kMaxChains; ++c)
                     ok = cudaStreamCreateWithFlags(&e->side[c], cudaStreamNonBlocking) == cudaSuccess &&
-                         cudaEventCreateWithFlags(&e->ev_join[c], cudaEventDisableTiming) == cudaSuccess;
+                         (c == EngineState::kMaxChains - 1 ||
+                          cudaEventCreateWithFlags(&e->ev_join[c], cudaEventDisableTiming) == cudaSuccess);
                 if (ok) {
                     const EngineState::Cfg d = e->configs[0];
                     e->configs.insert(e->configs.begin(), {d.first, d.second, 2});
@@ -2272,11 +2278,12 @@ int engine_create(const tts_system_desc &d, const std::vector<HostInstance> &hos
 void engine_destroy(EngineState *e)
 {
     if (!e) return;
-    for (int c = 0; c < EngineState::kMaxChains - 1; ++c) {
+    for (int c = 0; c < EngineState::kMaxChains; ++c)
         if (e->side[c]) cudaStreamDestroy(e->side[c]);
+    for (int c = 0; c < EngineState::kMaxChains - 1; ++c)
         if (e->ev_join[c]) cudaEventDestroy(e->ev_join[c]);
-    }
     if (e->ev_fork) cudaEventDestroy(e->ev_fork);
+    if (e->ev_ttm) cudaEventDestroy(e->ev_ttm);
     if (e->S1 && e->S1 != e->S) cudaFree(e->S1);
     for (void *q : {static_cast<void *>(e->cur), static_cast<void *>(e->done)})
         if (q) cudaFree(q);
@@ -2358,6 +2365,9 @@ PairArgs pair_args(const EngineState *e, const StepParams &p, const DevBuffers &
     a.cur = e->cur;
     a.cell = b.cell;
     a.sigma = static_cast<const float *>(b.sigma);
+    // with sigma_alternate the table of odd steps is sigma_alt, which follows
+    // sigma in the same allocation
+    a.sigma_odd = p.sigma_alternate ? static_cast<uint32_t>(static_cast<const float *>(b.sigma_alt) - a.sigma) : 0u;
     a.step = b.step;
     a.health = b.health;
     a.k = make_pair_consts(e, p, hsel);
@@ -2488,15 +2498,31 @@ cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuf
     }
     // instance chains of the FP32 separate passes (not for the merged sweep)
     const int chains = (e->pair && !fused && !p.merged && e->bx > 0) ? std::min(e->chains, e->n_inst) : 1;
+    // With chains, a one-sub-step TTM runs on a branch of its own beside the
+    // colour passes (it does not depend on the spins): it writes the next
+    // step's noise table into the table of that step's parity while the
+    // passes read the other, and the step counter advances after the passes.
+    // (Not while profiling: the colour passes are then timed on their own.)
+    const bool ttm_beside = chains > 1 && ttm_active && p.ttm_one_substep && !p.sigma_per_step &&
+                            tp.source != TTS_SOURCE_STEP_PROFILE && b.sigma_alt && b.cell_inst && !ev0;
+    StepParams q = p;
+    q.sigma_alternate = ttm_beside ? 1 : 0;
     if (chains > 1 && err == cudaSuccess) {
         err = cudaEventRecord(e->ev_fork, st);
         for (int c = 1; c < chains && err == cudaSuccess; ++c) err = cudaStreamWaitEvent(e->side[c - 1], e->ev_fork, 0);
+        cudaStream_t tst = e->side[chains - 1];
+        if (ttm_beside && err == cudaSuccess) {
+            err = cudaStreamWaitEvent(tst, e->ev_fork, 0);
+            if (err == cudaSuccess) err = launch_ttm(q, b, tp, p.n_instances, tst, e->precision, 0);
+            if (err == cudaSuccess) err = cudaEventRecord(e->ev_ttm, tst);
+            *kernels += 2;
+        }
         for (int pass = 0; pass < npass && err == cudaSuccess; ++pass) {
             const int c = pass < e->K - 1 ? pass : (pass == e->K - 1 ? e->K - 1 : 2 * e->K - 2 - pass);
             const int hsel = pass == e->K - 1 ? 1 : 0;
             int rbx, rby;
             row_block(e, rbx, rby);
-            PairArgs a = pair_args(e, p, b, hsel);
+            PairArgs a = pair_args(e, q, b, hsel);
             const auto fn = pair_kernel_fn(e->axis_z, false, pair_cell_mode(a));
             for (int ch = 0; ch < chains && err == cudaSuccess; ++ch) {
                 const int i0 = ch * e->n_inst / chains, i1 = (ch + 1) * e->n_inst / chains;
@@ -2575,6 +2601,8 @@ cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuf
         ++*kernels;
     }
     if (err == cudaSuccess && ev1) err = cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal);
+    // the TTM branch joins after the passes' end mark
+    if (ttm_beside && err == cudaSuccess) err = cudaStreamWaitEvent(st, e->ev_ttm, 0);
     bool partials = false;
     if (err == cudaSuccess && p.sample_every > 0 && !p.obs_skip) {
         if (e->pair) {
@@ -2592,8 +2620,10 @@ cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuf
         }
         ++*kernels;
     }
+    // (with the TTM beside the passes: only the observables or the bare step increment)
     if (err == cudaSuccess)
-        err = step_tail(p, b, tp, ttm_active, p.n_instances, e->precision, p.obs_blocks, st, kernels, partials);
+        err = step_tail(p, b, tp, ttm_active && !ttm_beside, p.n_instances, e->precision, p.obs_blocks, st, kernels,
+                        partials);
     return err;
 }
 

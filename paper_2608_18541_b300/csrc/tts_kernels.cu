@@ -316,13 +316,17 @@ template <typename R>
 __global__ void ttm_apply_kernel(StepParams p, DevBuffers b, TtmParams tp, int ncells_total, int inc_step)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (inc_step && g == 0) *b.step += 1;
+    // the table of the next step: sigma, or with sigma_alternate the one of
+    // that step's parity (the colour passes of this step may still read the
+    // other; the step counter is advanced after them)
+    R *out = static_cast<R *>(p.sigma_alternate && ((*b.step + 1) & 1) ? b.sigma_alt : b.sigma);
+    if (inc_step && !p.sigma_alternate && g == 0) *b.step += 1;
     if (g >= ncells_total) return;
     // electron energy gamma_e T^2 / 2 plus the increment, back to T
     const double T0 = b.Te[g];
     const double T = sqrt(fma(2.0 * b.ttm_scratch[g], tp.inv_gamma_e, T0 * T0));
     b.Te[g] = T;
-    write_sigma<R>(p, T, static_cast<R *>(b.sigma), g);
+    write_sigma<R>(p, T, out, g);
 }
 
 // Prescribed three-stage T_e (step profile) at time t.
@@ -615,12 +619,18 @@ static int cell_block(int64_t n) { return spread_block(n, 256); }
 
 cudaError_t launch_sigma(const StepParams &p, const DevBuffers &b, int ncells, int precision, cudaStream_t st)
 {
+    // both tables: whichever one a pass reads holds the noise of the current T_e
     const int bs = cell_block(ncells), gs = (ncells + bs - 1) / bs;
-    if (precision == 64)
-        sigma_kernel<double><<<gs, bs, 0, st>>>(p, b.Te, static_cast<double *>(b.sigma), ncells);
-    else
-        sigma_kernel<float><<<gs, bs, 0, st>>>(p, b.Te, static_cast<float *>(b.sigma), ncells);
-    return cudaGetLastError();
+    for (void *tab : {b.sigma, b.sigma_alt}) {
+        if (!tab) continue;
+        if (precision == 64)
+            sigma_kernel<double><<<gs, bs, 0, st>>>(p, b.Te, static_cast<double *>(tab), ncells);
+        else
+            sigma_kernel<float><<<gs, bs, 0, st>>>(p, b.Te, static_cast<float *>(tab), ncells);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_pass_general(const StepParams &p, const DevBuffers &b, int precision, int pass,

@@ -28,6 +28,9 @@ struct StepParams {
     int merged;              // merged (leapfrog) sweep (engines read it from here)
     int obs_skip;            // host-side: record this step without its observable kernels
                              // (a step the host knows does not sample)
+    int sigma_alternate;     // the TTM of this step runs beside its colour passes: it writes
+                             // the next step's noise table into the other of sigma / sigma_alt
+                             // (by the parity of that step) and leaves the step counter alone
     int64_t *lstep;          // lattice step counter (moving lattice)
     double *lat_partial;     // per observable block: kinetic and pair energy (moving lattice)
 };
@@ -41,6 +44,9 @@ struct DevBuffers {
     int *nbr = nullptr;           // zmax * n_total neighbour slots (column-major)
     void *nbr_w = nullptr;        // zmax * n_total J_ij / mu_i (tesla), real_t
     void *sigma = nullptr;        // ncells * 2 species * 2 (h = dt/2, dt), real_t
+    void *sigma_alt = nullptr;    // a second table of the same shape, right after sigma in its
+                                  // allocation: with sigma_alternate the table of step n is
+                                  // sigma (n even) or sigma_alt (n odd)
     double *Te = nullptr, *Tl = nullptr;   // per global cell
     double *src_shape = nullptr;  // per global cell
     double *ttm_scratch = nullptr;// 2 * ncells

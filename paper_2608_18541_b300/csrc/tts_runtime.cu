@@ -206,10 +206,11 @@ int upload_general(tts_system *s)
 int alloc_cells(tts_system *s, int ncells_total)
 {
     DevBuffers &b = s->b;
-    for (void *q : {(void *)b.Te, (void *)b.Tl, (void *)b.src_shape, (void *)b.ttm_scratch, b.sigma, (void *)b.cell_inst})
+    for (void *q : {(void *)b.Te, (void *)b.Tl, (void *)b.src_shape, (void *)b.ttm_scratch, b.sigma,
+                    (void *)b.cell_inst})
         if (q) cudaFree(q);
     b.Te = b.Tl = b.src_shape = b.ttm_scratch = nullptr;
-    b.sigma = nullptr;
+    b.sigma = b.sigma_alt = nullptr;
     b.cell_inst = nullptr;
     int rc;
     if ((rc = dev_alloc(&b.Te, ncells_total, "T_e"))) return rc;
@@ -217,9 +218,12 @@ int alloc_cells(tts_system *s, int ncells_total)
     if ((rc = dev_alloc(&b.src_shape, ncells_total, "source shape"))) return rc;
     if ((rc = dev_alloc(&b.ttm_scratch, 2 * size_t(ncells_total), "TTM scratch"))) return rc;
     if ((rc = dev_alloc(&b.cell_inst, ncells_total, "cell instances"))) return rc;
+    // the two noise tables (see DevBuffers::sigma_alt) in one allocation
     char *sig = nullptr;
-    if ((rc = dev_alloc(&sig, size_t(ncells_total) * TTS_MAX_SPECIES * 2 * s->rsize, "sigma table"))) return rc;
+    const size_t table = size_t(ncells_total) * TTS_MAX_SPECIES * 2 * s->rsize;
+    if ((rc = dev_alloc(&sig, 2 * table, "sigma tables"))) return rc;
     b.sigma = sig;
+    b.sigma_alt = sig + table;
     s->ncells_total = ncells_total;
     s->p.ncells_total = ncells_total;
     return TTS_OK;
@@ -1143,6 +1147,9 @@ int tts_set_config(tts_system *s, int index, int *current, int *n_configs)
         if (s->eng) engine_set_config(s->eng, index);
         else s->pass_block = s->pass_blocks[index];
         s->dirty = true;
+        // a configuration may read the other noise table: both from T_e
+        int rc = refresh_sigma(s);
+        if (rc) return rc;
     }
     if (current) {
         if (s->eng) *current = engine_config(s->eng);
@@ -1406,7 +1413,7 @@ int tts_set_step(tts_system *s, int64_t step)
     TTS_CUDA(cudaMemcpy(s->b.step, &step, sizeof(int64_t), cudaMemcpyHostToDevice), "write step");
     TTS_CUDA(cudaMemset(s->b.open, 0, sizeof(int)), "reset sweep state");
     s->host_step = step;
-    return TTS_OK;
+    return refresh_sigma(s);     // the table a pass reads may depend on the step's parity
 }
 
 static_assert(kHealthNonFinite == TTS_HEALTH_NONFINITE && kHealthTimeout == TTS_HEALTH_TIMEOUT &&
