@@ -180,8 +180,7 @@ struct PairArgs {
     ulonglong2 *S1;              // second state buffer of the fused sweep (= S without it)
     const int *cur;              // 1: the current state is in S1, else in S
     const int *cell;             // general slot -> TTM cell
-    const float *sigma;          // [cell][species][h]
-    uint32_t sigma_odd;          // elements from sigma to the table of odd steps (0: one table)
+    const float *sigma;          // [cell][species][h], the table of this launch's step
     const int64_t *step;
     unsigned int *health;
     PairConsts k;
@@ -347,7 +346,7 @@ template <bool AXZ, int CM = kCellAny>
 __device__ __forceinline__ void pair_finish(const PairArgs &a, const PairSite &p, int colour, int hsel, bool h2, f2 g1,
                                             f2 g2, f2 g3, f2 htx, f2 hty, f2 htz, f2 h1x, f2 h1y, f2 h1z,
                                             ulonglong2 olo, ulonglong2 ohi, ulonglong2 *Wlo, ulonglong2 *Whi,
-                                            uint32_t q, uint32_t step)
+                                            uint32_t q)
 {
     f2 sx{olo.x}, sy{olo.y}, sz{ohi.x};
     const f2 w{ohi.y};
@@ -358,8 +357,7 @@ __device__ __forceinline__ void pair_finish(const PairArgs &a, const PairSite &p
         const int tA = wA != 0.0f ? 1 : 0, tB = wB != 0.0f ? 1 : 0;
         int cA, cB;
         pair_cells<CM>(a, p, colour, cA, cB);
-        const float *tab = a.sigma + (step & 1u) * a.sigma_odd;
-        sig = f2_make(tab[(cA * TTS_MAX_SPECIES + tA) * 2 + hsel], tab[(cB * TTS_MAX_SPECIES + tB) * 2 + hsel]);
+        sig = f2_make(a.sigma[(cA * TTS_MAX_SPECIES + tA) * 2 + hsel], a.sigma[(cB * TTS_MAX_SPECIES + tB) * 2 + hsel]);
     }
     pair_update<AXZ>(sx, sy, sz, htx, hty, htz, h1x, h1y, h1z, w, a.noise != 0, sig, g1, g2, g3, a.k, h2);
     float sA, sB;
@@ -403,9 +401,8 @@ __device__ __forceinline__ void pair_block(const PairArgs &a, int colour, int hs
     }
     if (y2 >= Ly2 || kx >= hx) return;
     const PairSite p = make_site(a, inst, z, y2, kx, colour);
-    const uint32_t step = static_cast<uint32_t>(*a.step);
     f2 g1{0}, g2{0}, g3{0};
-    if (a.noise) site_noise(a, p, step, pass, g1, g2, g3);
+    if (a.noise) site_noise(a, p, static_cast<uint32_t>(*a.step), pass, g1, g2, g3);
     ulonglong2 *base = pair_state(a) + int64_t(inst) * a.n_inst_sites;
     const ulonglong2 *Olo = base + (colour ? 0 : a.nhalf);
     const ulonglong2 *Ohi = Olo + a.npair;
@@ -419,7 +416,7 @@ __device__ __forceinline__ void pair_block(const PairArgs &a, int colour, int hs
                    (z * Ly2 + yp) * hx, (z * Ly2 + ym) * hx, htx, hty, htz, h1x, h1y, h1z);
     const uint32_t q = r0 + kx;
     pair_finish<AXZ, CM>(a, p, colour, hsel, h2, g1, g2, g3, htx, hty, htz, h1x, h1y, h1z, Wlo[q], Whi[q], Wlo, Whi,
-                         q, step);
+                         q);
 }
 
 // SW: the launch is a leading or trailing pass of the merged sweep (compiled
@@ -577,7 +574,7 @@ __global__ void __launch_bounds__(256, 3) checker_pair_tiled_kernel(PairArgs a, 
                 const uint32_t qs = ty * hx + tx;
                 const uint32_t q = (z * Ly2 + y0 + ty) * hx + tx;
                 pair_finish<AXZ>(a, p, colour, hsel, h2, g1, g2, g3, htx, hty, htz, h1x, h1y, h1z, Tw[qs],
-                                 Tw[tw + qs], gw, gw + a.npair, q, step);
+                                 Tw[tw + qs], gw, gw + a.npair, q);
             }
             ++c_o;
             ++c_w;
@@ -2364,10 +2361,9 @@ PairArgs pair_args(const EngineState *e, const StepParams &p, const DevBuffers &
     a.S1 = static_cast<ulonglong2 *>(e->S1);
     a.cur = e->cur;
     a.cell = b.cell;
-    a.sigma = static_cast<const float *>(b.sigma);
-    // with sigma_alternate the table of odd steps is sigma_alt, which follows
-    // sigma in the same allocation
-    a.sigma_odd = p.sigma_alternate ? static_cast<uint32_t>(static_cast<const float *>(b.sigma_alt) - a.sigma) : 0u;
+    // with sigma_alternate the table of odd steps is sigma_alt; the parity of
+    // the step is fixed when the step is recorded
+    a.sigma = static_cast<const float *>(p.sigma_alternate && p.sigma_parity ? b.sigma_alt : b.sigma);
     a.step = b.step;
     a.health = b.health;
     a.k = make_pair_consts(e, p, hsel);
@@ -2447,6 +2443,15 @@ cudaError_t engine_obs_partials(EngineState *e, const StepParams &p, const DevBu
     return cudaGetLastError();
 }
 
+bool engine_step_parity(const EngineState *e, const StepParams &p, const DevBuffers &b, const TtmParams &tp,
+                        bool ttm_active)
+{
+    const bool chains = e->engine == TTS_ENGINE_CHECKER && e->pair && !p.merged && e->bx > 0 &&
+                        std::min(e->chains, e->n_inst) > 1;
+    return chains && ttm_active && p.ttm_one_substep && !p.sigma_per_step && tp.source != TTS_SOURCE_STEP_PROFILE &&
+           b.sigma_alt && b.cell_inst;
+}
+
 cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuffers &b, const TtmParams &tp,
                                bool ttm_active, cudaStream_t st, int *kernels, cudaEvent_t ev0, cudaEvent_t ev1)
 {
@@ -2503,8 +2508,7 @@ cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuf
     // step's noise table into the table of that step's parity while the
     // passes read the other, and the step counter advances after the passes.
     // (Not while profiling: the colour passes are then timed on their own.)
-    const bool ttm_beside = chains > 1 && ttm_active && p.ttm_one_substep && !p.sigma_per_step &&
-                            tp.source != TTS_SOURCE_STEP_PROFILE && b.sigma_alt && b.cell_inst && !ev0;
+    const bool ttm_beside = engine_step_parity(e, p, b, tp, ttm_active) && !ev0;
     StepParams q = p;
     q.sigma_alternate = ttm_beside ? 1 : 0;
     if (chains > 1 && err == cudaSuccess) {

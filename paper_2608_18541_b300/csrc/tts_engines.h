@@ -33,6 +33,11 @@ const char *engine_last_error();
 cudaError_t engine_record_step(EngineState *e, const StepParams &p, const DevBuffers &b, const TtmParams &tp,
                                bool ttm_active, cudaStream_t st, int *kernels, cudaEvent_t ev_begin,
                                cudaEvent_t ev_end);
+// The steps this engine records differ by the parity of their step (the TTM
+// beside the colour passes, on noise tables alternated by parity): a recorded
+// step is replayed only at the parity StepParams::sigma_parity names.
+bool engine_step_parity(const EngineState *e, const StepParams &p, const DevBuffers &b, const TtmParams &tp,
+                        bool ttm_active);
 // Engines that advance many steps in one launch (resident): run nsteps steps.
 bool engine_multi_step(const EngineState *e);
 cudaError_t engine_run_steps(EngineState *e, const StepParams &p, const DevBuffers &b, const TtmParams &tp,

@@ -319,7 +319,7 @@ __global__ void ttm_apply_kernel(StepParams p, DevBuffers b, TtmParams tp, int n
     // the table of the next step: sigma, or with sigma_alternate the one of
     // that step's parity (the colour passes of this step may still read the
     // other; the step counter is advanced after them)
-    R *out = static_cast<R *>(p.sigma_alternate && ((*b.step + 1) & 1) ? b.sigma_alt : b.sigma);
+    R *out = static_cast<R *>(p.sigma_alternate && !p.sigma_parity ? b.sigma_alt : b.sigma);
     if (inc_step && !p.sigma_alternate && g == 0) *b.step += 1;
     if (g >= ncells_total) return;
     // electron energy gamma_e T^2 / 2 plus the increment, back to T

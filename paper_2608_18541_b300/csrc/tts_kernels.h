@@ -31,6 +31,8 @@ struct StepParams {
     int sigma_alternate;     // the TTM of this step runs beside its colour passes: it writes
                              // the next step's noise table into the other of sigma / sigma_alt
                              // (by the parity of that step) and leaves the step counter alone
+    int sigma_parity;        // with sigma_alternate: the parity of this step (fixed when the
+                             // step is recorded; its graph is replayed only at that parity)
     int64_t *lstep;          // lattice step counter (moving lattice)
     double *lat_partial;     // per observable block: kinetic and pair energy (moving lattice)
 };

@@ -244,12 +244,14 @@ SweepCtl sweep_ctl(const tts_system *s, int pass, int npass)
     return w;
 }
 
-cudaError_t record_step(tts_system *s, cudaStream_t c, int *kernels, cudaEvent_t ev0, cudaEvent_t ev1, bool obs)
+cudaError_t record_step(tts_system *s, cudaStream_t c, int *kernels, cudaEvent_t ev0, cudaEvent_t ev1, bool obs,
+                        int64_t step)
 {
     *kernels = 0;
     if (s->lat) return lattice_record_step(s, c, kernels, ev0, ev1);
     StepParams p = s->p;
     p.obs_skip = obs ? 0 : 1;
+    p.sigma_parity = static_cast<int>(step & 1);
     if (s->eng) {
         p.merged = s->merged ? 1 : 0;
         return engine_record_step(s->eng, p, s->b, s->tp, s->ttm_active, c, kernels, ev0, ev1);
@@ -274,10 +276,22 @@ cudaError_t record_step(tts_system *s, cudaStream_t c, int *kernels, cudaEvent_t
     return e;
 }
 
-// Capture nsteps steps into one graph.  obs: 0 = every step without its
-// observable kernels, 1 = every step with them, 2 = only the last step with
-// them.  *kernels_out = kernels per replay.
-int capture_steps(tts_system *s, int nsteps, int obs, cudaGraphExec_t *out, int *kernels_out)
+void destroy_graphs(tts_system *s)
+{
+    for (cudaGraphExec_t *set : {s->graph, s->graph_multi, s->graph_plain, s->graph_cycle})
+        for (int v = 0; v < 2; ++v)
+            if (set[v]) {
+                cudaGraphExecDestroy(set[v]);
+                set[v] = nullptr;
+            }
+    s->by_parity = false;
+}
+
+// Capture nsteps steps into one graph, to be replayed from steps of the
+// parity of step0.  obs: 0 = every step without its observable kernels, 1 =
+// every step with them, 2 = only the last step with them.  *kernels_out =
+// kernels per replay.
+int capture_steps(tts_system *s, int nsteps, int obs, int64_t step0, cudaGraphExec_t *out, int *kernels_out)
 {
     cudaStream_t c = s->capture;
     TTS_CUDA(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -285,7 +299,7 @@ int capture_steps(tts_system *s, int nsteps, int obs, cudaGraphExec_t *out, int 
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < nsteps && e == cudaSuccess; ++i) {
         int kernels = 0;
-        e = record_step(s, c, &kernels, nullptr, nullptr, obs == 1 || (obs == 2 && i == nsteps - 1));
+        e = record_step(s, c, &kernels, nullptr, nullptr, obs == 1 || (obs == 2 && i == nsteps - 1), step0 + i);
         total += kernels;
     }
     cudaGraph_t g = nullptr;
@@ -307,11 +321,7 @@ constexpr int kMaxCycleSteps = 256;
 
 int build_graph(tts_system *s)
 {
-    for (cudaGraphExec_t *g : {&s->graph, &s->graph_multi, &s->graph_plain, &s->graph_cycle})
-        if (*g) {
-            cudaGraphExecDestroy(*g);
-            *g = nullptr;
-        }
+    destroy_graphs(s);
     // a moving lattice has ~100 kernels per step: fewer steps per graph
     s->graph_steps = s->lat ? 4 : 16;
     // While sampling, graphs follow the sampling phase (tts_schedule.h); a
@@ -319,13 +329,18 @@ int build_graph(tts_system *s)
     // kernels in every step.
     s->phased = !s->lat && s->p.sample_every > 0;
     s->cycle_steps = 0;
-    int rc = capture_steps(s, 1, 1, &s->graph, &s->kernels_graph);
-    if (!rc) rc = capture_steps(s, s->graph_steps, s->phased ? 0 : 1, &s->graph_multi, &s->kernels_multi);
-    if (!rc && s->phased) rc = capture_steps(s, 1, 0, &s->graph_plain, &s->kernels_plain);
-    if (!rc && s->phased && s->p.sample_every >= 2 && s->p.sample_every <= kMaxCycleSteps) {
-        rc = capture_steps(s, s->p.sample_every, 2, &s->graph_cycle, &s->kernels_cycle);
-        if (!rc) s->cycle_steps = s->p.sample_every;
+    StepParams q = s->p;
+    q.merged = s->merged ? 1 : 0;
+    s->by_parity = !s->lat && s->eng && engine_step_parity(s->eng, q, s->b, s->tp, s->ttm_active);
+    const bool cycle = s->phased && s->p.sample_every >= 2 && s->p.sample_every <= kMaxCycleSteps;
+    int rc = TTS_OK;
+    for (int v = 0; v < (s->by_parity ? 2 : 1) && !rc; ++v) {
+        rc = capture_steps(s, 1, 1, v, &s->graph[v], &s->kernels_graph);
+        if (!rc) rc = capture_steps(s, s->graph_steps, s->phased ? 0 : 1, v, &s->graph_multi[v], &s->kernels_multi);
+        if (!rc && s->phased) rc = capture_steps(s, 1, 0, v, &s->graph_plain[v], &s->kernels_plain);
+        if (!rc && cycle) rc = capture_steps(s, s->p.sample_every, 2, v, &s->graph_cycle[v], &s->kernels_cycle);
     }
+    if (cycle && !rc) s->cycle_steps = s->p.sample_every;
     if (rc) return rc;
     s->dirty = false;
     return TTS_OK;
@@ -456,8 +471,7 @@ int tts_destroy(tts_system *s)
 {
     if (!s) return TTS_OK;
     cudaStreamSynchronize(s->stream);
-    for (cudaGraphExec_t g : {s->graph, s->graph_multi, s->graph_plain, s->graph_cycle})
-        if (g) cudaGraphExecDestroy(g);
+    destroy_graphs(s);
     drop_profile_events(s);
     if (s->eng) engine_destroy(s->eng);
     if (s->lat) lattice_destroy(s->lat);
@@ -1014,7 +1028,7 @@ int tts_step(tts_system *s, int64_t nsteps)
             if (e != cudaSuccess) break;
             s->prof_pair_steps.push_back(1);
             int kernels = 0;
-            e = record_step(s, c, &kernels, ev[0], ev[1], true);
+            e = record_step(s, c, &kernels, ev[0], ev[1], true, step0 + i);
             total += kernels;
         }
         cudaGraph_t g = nullptr;
@@ -1037,31 +1051,36 @@ int tts_step(tts_system *s, int64_t nsteps)
         int rc = build_graph(s);
         if (rc) return rc;
     }
+    // the graph variant of the parity of the step it starts at
+    int64_t at = step0;
+    auto var = [&]() { return s->by_parity ? static_cast<int>(at & 1) : 0; };
     if (!s->phased) {
         int64_t left = nsteps;
-        for (; left >= s->graph_steps; left -= s->graph_steps) {
-            TTS_CUDA(cudaGraphLaunch(s->graph_multi, s->stream), "launch step graph");
+        for (; left >= s->graph_steps; left -= s->graph_steps, at += s->graph_steps) {
+            TTS_CUDA(cudaGraphLaunch(s->graph_multi[var()], s->stream), "launch step graph");
             s->launches += s->kernels_multi;
         }
-        for (; left > 0; --left) {
-            TTS_CUDA(cudaGraphLaunch(s->graph, s->stream), "launch step graph");
+        for (; left > 0; --left, ++at) {
+            TTS_CUDA(cudaGraphLaunch(s->graph[var()], s->stream), "launch step graph");
             s->launches += s->kernels_graph;
         }
         return TTS_OK;
     }
     cudaError_t err = cudaSuccess;
-    schedule_steps(step0, nsteps, s->p.sample_every, s->graph_steps, s->cycle_steps, [&](StepGraph g, int64_t) {
+    schedule_steps(step0, nsteps, s->p.sample_every, s->graph_steps, s->cycle_steps, [&](StepGraph g, int64_t n) {
         if (err != cudaSuccess) return;
-        cudaGraphExec_t x = s->graph;
+        const int v = var();
+        at += n;
+        cudaGraphExec_t x = s->graph[v];
         int k = s->kernels_graph;
         if (g == StepGraph::Cycle) {
-            x = s->graph_cycle;
+            x = s->graph_cycle[v];
             k = s->kernels_cycle;
         } else if (g == StepGraph::PlainRun) {
-            x = s->graph_multi;
+            x = s->graph_multi[v];
             k = s->kernels_multi;
         } else if (g == StepGraph::Plain) {
-            x = s->graph_plain;
+            x = s->graph_plain[v];
             k = s->kernels_plain;
         }
         err = cudaGraphLaunch(x, s->stream);
@@ -1134,7 +1153,8 @@ int tts_autotune(tts_system *s, int probe_steps, int *chosen, int *n_configs)
     else s->pass_block = s->pass_blocks[best];
     s->dirty = true;
     if (chosen) *chosen = best;
-    return TTS_OK;
+    // the chosen configuration may read the other noise table: both from T_e
+    return refresh_sigma(s);
 }
 
 int tts_set_config(tts_system *s, int index, int *current, int *n_configs)
@@ -1171,7 +1191,9 @@ int tts_profile_enable(tts_system *s, int enable)
     s->prof_ms = 0.0;
     s->prof_steps = 0;
     s->profiling = enable != 0;
-    return TTS_OK;
+    // profiled steps keep the TTM after the passes and one noise table: both
+    // tables from T_e, whichever the next step reads
+    return refresh_sigma(s);
 }
 
 int tts_profile_read(tts_system *s, double *ms, int64_t *steps, int64_t *spin_steps)

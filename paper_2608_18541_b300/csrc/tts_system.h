@@ -80,10 +80,13 @@ struct tts_system {
     int obs_capacity = 1024;
     tts::DevBuffers b;
     tts::StepParams p{};
-    cudaGraphExec_t graph = nullptr;        // one step (with its observable kernels, if sampling)
-    cudaGraphExec_t graph_multi = nullptr;  // graph_steps steps (without them, if sampling)
-    cudaGraphExec_t graph_plain = nullptr;  // sampling only: one step without them
-    cudaGraphExec_t graph_cycle = nullptr;  // sampling only: one sampling interval, them in its last step
+    // Step graphs, by the parity of the step they start at ([1] only when the
+    // recorded steps depend on it: the noise tables alternated by parity)
+    cudaGraphExec_t graph[2] = {};          // one step (with its observable kernels, if sampling)
+    cudaGraphExec_t graph_multi[2] = {};    // graph_steps steps (without them, if sampling)
+    cudaGraphExec_t graph_plain[2] = {};    // sampling only: one step without them
+    cudaGraphExec_t graph_cycle[2] = {};    // sampling only: one sampling interval, them in its last step
+    bool by_parity = false;                 // the [1] graphs exist
     int graph_steps = 16;
     int cycle_steps = 0;                    // steps of graph_cycle (0: none)
     int kernels_graph = 0, kernels_multi = 0, kernels_plain = 0, kernels_cycle = 0;   // per replay

@@ -58,3 +58,26 @@ def test_profiled_pass_time_fits_the_step():
     assert g.info().kernel_launches - k0 >= 200 * 6     # three passes on each of two instance chains
     pass_ms = ms / steps
     assert 0.0 < pass_ms <= 1.25 * step_ms, (pass_ms, step_ms)
+
+
+def test_mode_switches_at_odd_steps_keep_the_trajectory():
+    """The step graphs run the TTM beside the colour passes on noise tables
+    alternated by step parity; profiled steps and single-chain configurations
+    keep one table.  Switching between them after an odd number of steps must
+    leave the trajectory bitwise unchanged."""
+    a, b = _system(), _system()
+    a.step(31)
+    b.step(7)                        # graphs from an even step
+    b.profile_enable(True)
+    b.step(5)                        # profiled, from an odd step
+    b.profile_enable(False)
+    b.step(3)                        # graphs from an even step again
+    _, n = b.set_config(-1)
+    for c in (1, 0, n - 1, 0):       # a single chain, two chains, the last configuration
+        b.set_config(c)
+        b.step(3)                    # ends on steps 18, 21, 24, 27
+    b.step(4)
+    assert b.get_step() == 31
+    for i in range(2):
+        assert np.array_equal(a.get_spins(i), b.get_spins(i))
+    assert np.array_equal(a.observables(0), b.observables(0))
